@@ -1,0 +1,204 @@
+"""Reference oracle for MoCHy motif counting (TEST INFRASTRUCTURE ONLY).
+
+A plain, slow, single-threaded C++ restatement of the paper's algorithms
+(``mochy_oracle.cpp``), loaded with ctypes.  Only the test suite, the smoke
+check and the bench's CPU-baseline leg may import this package; the CUDA
+library never does, and this package never imports the library.
+
+Functions whose parity is pinned by tests/test_oracle_*.py:
+  tables, count_kh           motif tables and the kh-motif chain
+  philox                     Philox4x32-10 known answers
+  dedupe, project            load and line-graph construction
+  count_exact, count_exact_subset
+  count_sampled              MoCHy-A / MoCHy-A+
+  randomize, profile         Chung-Lu null model, significance, CP
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mochy_oracle.cpp")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+N_H, N_3H = 26, 431
+A, A_PLUS = 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host compiler (plain -O2, one thread)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC",
+                           "-o", tmp, _SRC])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            _lib.orc_count_kh.restype = ctypes.c_int64
+            _lib.orc_count_kh.argtypes = [ctypes.c_int]
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _csr(offsets, nodes):
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nod = np.ascontiguousarray(nodes, dtype=np.int32)
+    if nod.size == 0:
+        nod = np.zeros(1, np.int32)
+    return off, nod
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with code {rc}")
+
+
+def tables():
+    """Motif tables: dict of lut_h[128], lut_3h[2187], patterns, t_to_h, open."""
+    lib = _load()
+    lut_h = np.zeros(128, np.int32)
+    lut_3h = np.zeros(2187, np.int32)
+    hp = np.zeros((N_H, 7), np.uint8)
+    tp = np.zeros((N_3H, 7), np.uint8)
+    t2h = np.zeros(N_3H, np.int32)
+    hopen = np.zeros(N_H, np.uint8)
+    chain = np.zeros(8, np.int64)
+    _check(lib.orc_tables(_p(lut_h), _p(lut_3h), _p(hp), _p(tp), _p(t2h), _p(hopen),
+                          _p(chain)), "tables")
+    return dict(lut_h=lut_h, lut_3h=lut_3h, h_pattern=hp, t_pattern=tp, t_to_h=t2h,
+                h_open=hopen, chain=chain)
+
+
+def count_kh(k: int) -> int:
+    return int(_load().orc_count_kh(int(k)))
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    o = np.zeros(4, np.uint32)
+    _check(_load().orc_philox(_p(c), _p(k), _p(o)), "philox")
+    return o
+
+
+def dedupe(offsets, nodes):
+    off, nod = _csr(offsets, nodes)
+    e = off.size - 1
+    out_off = np.zeros(e + 1, np.int64)
+    out_nodes = np.zeros(max(nod.size, 1), np.int32)
+    n_out = np.zeros(1, np.int64)
+    n_dup = np.zeros(1, np.int64)
+    _check(_load().orc_dedupe(ctypes.c_int64(e), _p(off), _p(nod), _p(out_off),
+                              _p(out_nodes), _p(n_out), _p(n_dup)), "dedupe")
+    n = int(n_out[0])
+    return out_off[:n + 1].copy(), out_nodes[:out_off[n]].copy(), int(n_dup[0])
+
+
+def project(offsets, nodes):
+    """(|wedges|, max line-graph degree, degrees[E])."""
+    off, nod = _csr(offsets, nodes)
+    e = off.size - 1
+    nw = np.zeros(1, np.int64)
+    md = np.zeros(1, np.int64)
+    deg = np.zeros(max(e, 1), np.int64)
+    _check(_load().orc_project(ctypes.c_int64(e), _p(off), _p(nod), _p(nw), _p(md),
+                               _p(deg)), "project")
+    return int(nw[0]), int(md[0]), deg[:e]
+
+
+def count_exact(offsets, nodes, theta: int = 1):
+    off, nod = _csr(offsets, nodes)
+    h = np.zeros(N_H, np.int64)
+    h3 = np.zeros(N_3H, np.int64)
+    _check(_load().orc_count_exact(ctypes.c_int64(off.size - 1), _p(off), _p(nod),
+                                   ctypes.c_int32(theta), _p(h), _p(h3)), "count_exact")
+    return h, h3
+
+
+def count_exact_subset(offsets, nodes, anchors, theta: int = 1):
+    off, nod = _csr(offsets, nodes)
+    anc = np.ascontiguousarray(anchors, dtype=np.int32)
+    h = np.zeros(N_H, np.int64)
+    h3 = np.zeros(N_3H, np.int64)
+    _check(_load().orc_count_exact_subset(
+        ctypes.c_int64(off.size - 1), _p(off), _p(nod), ctypes.c_int32(theta),
+        _p(anc if anc.size else np.zeros(1, np.int32)), ctypes.c_int64(anc.size),
+        _p(h), _p(h3)), "count_exact_subset")
+    return h, h3
+
+
+def count_sampled(offsets, nodes, method: int, samples: int, seed: int, theta: int = 1):
+    off, nod = _csr(offsets, nodes)
+    rh = np.zeros(N_H, np.int64)
+    r3 = np.zeros(N_3H, np.int64)
+    eh = np.zeros(N_H, np.float64)
+    e3 = np.zeros(N_3H, np.float64)
+    _check(_load().orc_count_sampled(
+        ctypes.c_int64(off.size - 1), _p(off), _p(nod), ctypes.c_int32(theta),
+        ctypes.c_int(method), ctypes.c_int64(samples), ctypes.c_uint64(seed),
+        _p(rh), _p(r3), _p(eh), _p(e3)), "count_sampled")
+    return rh, r3, eh, e3
+
+
+def count_all_anchors(offsets, nodes, method: int, theta: int = 1):
+    """Sampling bodies run once per hyperedge (A) or per hyperwedge (A+)."""
+    off, nod = _csr(offsets, nodes)
+    rh = np.zeros(N_H, np.int64)
+    r3 = np.zeros(N_3H, np.int64)
+    _check(_load().orc_count_all_anchors(ctypes.c_int64(off.size - 1), _p(off), _p(nod),
+                                         ctypes.c_int32(theta), ctypes.c_int(method),
+                                         _p(rh), _p(r3)), "count_all_anchors")
+    return rh, r3
+
+
+def randomize(n_nodes: int, offsets, nodes, seed: int, copy: int):
+    off, nod = _csr(offsets, nodes)
+    e = off.size - 1
+    out_off = np.zeros(e + 1, np.int64)
+    out_nodes = np.zeros(max(nod.size, 1), np.int32)
+    n_out = np.zeros(1, np.int64)
+    _check(_load().orc_randomize(ctypes.c_int64(n_nodes), ctypes.c_int64(e), _p(off),
+                                 _p(nod), ctypes.c_uint64(seed), ctypes.c_uint32(copy),
+                                 _p(out_off), _p(out_nodes), _p(n_out)), "randomize")
+    n = int(n_out[0])
+    return out_off[:n + 1].copy(), out_nodes[:out_off[n]].copy()
+
+
+def profile(n_nodes: int, offsets, nodes, n_random: int, seed: int, theta: int = 1,
+            eps: float = 1.0):
+    """Significance and CP; also the per-graph counts (row 0 = input)."""
+    off, nod = _csr(offsets, nodes)
+    sig_h = np.zeros(N_H)
+    cp_h = np.zeros(N_H)
+    sig_3h = np.zeros(N_3H)
+    cp_3h = np.zeros(N_3H)
+    ch = np.zeros((1 + n_random, N_H), np.int64)
+    c3 = np.zeros((1 + n_random, N_3H), np.int64)
+    deg = np.zeros(2, np.int32)
+    _check(_load().orc_profile(
+        ctypes.c_int64(n_nodes), ctypes.c_int64(off.size - 1), _p(off), _p(nod),
+        ctypes.c_int32(theta), ctypes.c_int32(n_random), ctypes.c_uint64(seed),
+        ctypes.c_double(eps), _p(sig_h), _p(cp_h), _p(sig_3h), _p(cp_3h), _p(ch),
+        _p(c3), _p(deg)), "profile")
+    return dict(sig_h=sig_h, cp_h=cp_h, sig_3h=sig_3h, cp_3h=cp_3h, counts_h=ch,
+                counts_3h=c3, degenerate=deg)
