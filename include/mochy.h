@@ -1,0 +1,185 @@
+/*
+ * libmochy: GB300 (sm_103a) counting of hypergraph motifs (h-motifs) and
+ * ternary hypergraph motifs (3h-motifs), after "Hypergraph motifs and their
+ * extensions beyond binary" (arXiv 2310.15668).
+ *
+ * Plain C ABI.  Pointers named h_* are host memory, d_* device memory of the
+ * context's GPU.  Every call returns MOCHY_OK (0) or a negative MOCHY_E_*
+ * code; no exception or abort crosses the ABI.  mochy_last_error() gives a
+ * one-line message for the calling thread's last failure.
+ *
+ * Ownership: input arrays stay owned by the caller and are copied; output
+ * arrays are allocated by the caller with the stated sizes.  Device memory is
+ * owned by the context and freed by mochy_destroy.  A context is used by one
+ * host thread at a time.
+ *
+ * Limits: at most 2^26 - 1 hyperedges, 2^31 - 1 nodes, 63 nodes per
+ * hyperedge; exact counting needs at most 786,432 hyperedges (the per-row
+ * adjacency of the line graph is staged in shared memory).  A call outside
+ * these limits returns MOCHY_E_UNSUPPORTED.
+ *
+ * Motif ids: h-motifs are numbered 1..26, 3h-motifs 1..431 (arrays are
+ * indexed id-1).  The paper's figures that fix the numbering are lost; the
+ * numbering used here is: canonical pattern = lexicographically smallest
+ * region tuple (regions (1)..(7) of Section 2.2) over the six orders of the
+ * three hyperedges; h-motifs 1-16 are closed with a non-empty triple region,
+ * 17-22 open, 23-26 closed with an empty triple region, each group in
+ * ascending canonical tuple order; 3h-motifs are in ascending (h-motif id,
+ * canonical ternary tuple) order.  mochy_motif_pattern() returns the pattern
+ * of an id.
+ */
+#ifndef MOCHY_H
+#define MOCHY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MOCHY_OK 0
+#define MOCHY_E_INVALID (-1)        /* bad argument or malformed hypergraph */
+#define MOCHY_E_NOMEM (-2)          /* device allocation failed or over budget */
+#define MOCHY_E_CUDA (-3)           /* a CUDA call failed */
+#define MOCHY_E_TIMEOUT (-4)        /* a bounded device wait ran out */
+#define MOCHY_E_NOT_PROJECTED (-5)  /* the call needs mochy_project first */
+#define MOCHY_E_UNSUPPORTED (-6)    /* outside the limits above */
+#define MOCHY_E_BUSY (-7)           /* serving queue full */
+#define MOCHY_W_DEGENERATE_CP 1     /* success, but every significance is 0 */
+
+#define MOCHY_N_H 26
+#define MOCHY_N_3H 431
+#define MOCHY_MAX_EDGE_SIZE 63
+#define MOCHY_MAX_EDGES ((1 << 26) - 1)
+
+#define MOCHY_A 1       /* MoCHy-A: hyperedge sampling (Algorithm "sampling_ver1") */
+#define MOCHY_A_PLUS 2  /* MoCHy-A+: hyperwedge sampling (Algorithm "sampling_ver2") */
+
+typedef struct mochy_ctx mochy_ctx;
+
+typedef struct {
+  int32_t theta;            /* 3h-motif threshold theta >= 1 (Section 4.1); 1 */
+  double eps;               /* epsilon of Eq. "significance"; 1.0 */
+  int64_t hbm_budget_bytes; /* device bytes the context may hold; 0 = no cap */
+  int32_t device;           /* CUDA device ordinal; 0 */
+  void* stream;             /* cudaStream_t to run on; NULL = own stream */
+} mochy_config;
+
+/* Fill *cfg with the defaults above. */
+void mochy_config_default(mochy_config* cfg);
+
+/* Create a context on cfg->device (cfg may be NULL for defaults).  Builds the
+ * motif lookup tables on the device.  *out receives the handle. */
+int mochy_create(mochy_ctx** out, const mochy_config* cfg);
+
+/* Free the context and all its device memory.  NULL is accepted. */
+int mochy_destroy(mochy_ctx* ctx);
+
+/* Load a hypergraph G = (V, E) (Section 2.1).  Hyperedge i lists nodes
+ * h_edge_nodes[h_edge_offsets[i] .. h_edge_offsets[i+1]) (host int64 offsets,
+ * n_edges + 1 of them, starting at 0; int32 node ids in [0, n_nodes)).  A
+ * hyperedge must be non-empty and list each node once, in any order.  E is a
+ * set (Section 2.1 footnote): repeated hyperedges are dropped, the first
+ * occurrence is kept, and hyperedge ids are positions after that removal.
+ * Any previous hypergraph and line graph of ctx are released.
+ * *n_duplicates_removed (may be NULL) receives the number dropped.
+ * Errors: MOCHY_E_INVALID for malformed input, MOCHY_E_UNSUPPORTED past the
+ * limits. */
+int mochy_load(mochy_ctx* ctx, int64_t n_nodes, int64_t n_edges,
+               const int64_t* h_edge_offsets, const int32_t* h_edge_nodes,
+               int64_t* n_duplicates_removed);
+
+/* As mochy_load, with the two arrays already in device memory (not kept). */
+int mochy_load_device(mochy_ctx* ctx, int64_t n_nodes, int64_t n_edges,
+                      const int64_t* d_edge_offsets, const int32_t* d_edge_nodes,
+                      int64_t* n_duplicates_removed);
+
+/* Number of hyperedges and node-list length of the loaded hypergraph; with
+ * non-NULL host arrays (n_edges + 1 and n_incidences entries) also copies
+ * the deduplicated CSR out (node lists sorted ascending). */
+int mochy_get_hypergraph(mochy_ctx* ctx, int64_t* n_nodes, int64_t* n_edges,
+                         int64_t* n_incidences, int64_t* h_edge_offsets,
+                         int32_t* h_edge_nodes);
+
+/* Build the line graph (Section 2.1 "Line Graph"; Algorithm
+ * "hyperwedge_counting", Section 3.1): for every hyperedge e_i the sorted
+ * list of adjacent e_j with omega = |e_i & e_j|.  Kept on the device.
+ * *n_wedges = |wedges| (hyperwedges), *max_line_degree = max |N_{e_i}|
+ * (either may be NULL).  Needs enough device memory for 16 bytes per
+ * hyperwedge. */
+int mochy_project(mochy_ctx* ctx, int64_t* n_wedges, int32_t* max_line_degree);
+
+/* Copy |N_{e_i}| for every hyperedge to h_degrees (n_edges int64). */
+int mochy_line_degrees(mochy_ctx* ctx, int64_t* h_degrees);
+
+/* Exact counts (MoCHy-E, Algorithm "exact_motif_counting", Section 3.2):
+ * out_h[t-1] = number of instances of h-motif t, out_3h[t-1] of 3h-motif t
+ * (Section 4.1, threshold cfg.theta).  Needs mochy_project. */
+int mochy_count_exact(mochy_ctx* ctx, int64_t out_h[MOCHY_N_H],
+                      int64_t out_3h[MOCHY_N_3H]);
+
+/* The part of the exact count that Algorithm "exact_motif_counting" adds in
+ * the outer-loop iterations of the hyperedges h_anchors[0..n_anchors)
+ * (host int32 ids; an id may not repeat): open instances centred at an
+ * anchor plus closed instances whose smallest id is an anchor.  Summed over
+ * all hyperedges it equals mochy_count_exact. */
+int mochy_count_exact_subset(mochy_ctx* ctx, const int32_t* h_anchors,
+                             int64_t n_anchors, int64_t out_h[MOCHY_N_H],
+                             int64_t out_3h[MOCHY_N_3H]);
+
+/* Sampled counts.  method MOCHY_A draws `samples` hyperedges uniformly with
+ * replacement (Algorithm "sampling_ver1"); MOCHY_A_PLUS draws `samples`
+ * hyperwedges (Algorithm "sampling_ver2").  Draw n uses Philox4x32-10 with
+ * counter (n_lo, n_hi, stream, 0), key (seed_lo, seed_hi), stream 1 for A and
+ * 2 for A+, and maps the 64-bit output u to floor(u * range / 2^64);
+ * hyperwedges are indexed in ascending (i, j), i < j.  raw_* receive the
+ * int64 per-motif increments, est_* the unbiased estimates
+ * raw * |E| / (3 samples) (A) or raw * |wedges| / (w[t] samples) (A+, w = 2
+ * for open and 3 for closed motifs, Eq. "wt").  Output pointers may be NULL. */
+int mochy_count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t seed,
+                        int64_t raw_h[MOCHY_N_H], int64_t raw_3h[MOCHY_N_3H],
+                        double est_h[MOCHY_N_H], double est_3h[MOCHY_N_3H]);
+
+/* One randomized hypergraph of the paper's null model into a new context
+ * *out (same config): Chung-Lu on the incidence graph (Algorithm
+ * "randomized_hypergraph_alg", Appendix "Randomized Hypergraphs") followed by
+ * the set transform (Algorithm "transform"), empty hyperedges dropped and
+ * repeated hyperedges dropped keeping the first.  Draw d of copy c uses
+ * Philox4x32-10 with counter (d_lo, d_hi, 3 or 4, c) and key (seed); node
+ * and hyperedge endpoints are chosen with probability proportional to degree
+ * through integer prefix sums.  The copy is not projected. */
+int mochy_randomize(mochy_ctx* src, uint64_t seed, uint32_t copy, mochy_ctx** out);
+
+/* Significance and characteristic profile (Eq. "significance", Eq. "cp",
+ * Section 3.1) of the loaded hypergraph against n_random randomized copies
+ * (copies 0..n_random-1 of mochy_randomize with this seed), all counted
+ * exactly; M_rand is the mean over copies.  FP64.  counts_h / counts_3h
+ * (may be NULL) receive (1 + n_random) rows, the input first.  Returns
+ * MOCHY_W_DEGENERATE_CP (and zero CPs) when all significances are 0. */
+int mochy_profile(mochy_ctx* ctx, int32_t n_random, uint64_t seed,
+                  double sig_h[MOCHY_N_H], double cp_h[MOCHY_N_H],
+                  double sig_3h[MOCHY_N_3H], double cp_3h[MOCHY_N_3H],
+                  int64_t* counts_h, int64_t* counts_3h);
+
+/* Region pattern of motif `id` (kind 2: h-motif, kind 3: 3h-motif): states
+ * of regions (1)..(7) of Section 2.2 (0 empty, 1 at most theta nodes, 2 more;
+ * h-motifs use 0/1). */
+int mochy_motif_pattern(int kind, int32_t id, uint8_t regions_out[7]);
+
+/* cudaStream_t the context runs on (as void*), for event timing. */
+void* mochy_stream(mochy_ctx* ctx);
+
+/* Bytes of device memory the context holds now. */
+int64_t mochy_device_bytes(mochy_ctx* ctx);
+
+/* Number of kernels the library launched in this process (for accounting). */
+int64_t mochy_kernel_launches(void);
+
+const char* mochy_strerror(int code);
+const char* mochy_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOCHY_H */

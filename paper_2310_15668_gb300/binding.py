@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libmochy (include/mochy.h).
+
+Functions carry the C names and only marshal arguments: numpy arrays in,
+numpy arrays out, negative return codes raised as MochyError.  Every step of
+the computation runs in the CUDA library; if the library is missing, loading
+it fails loudly (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmochy.so")
+
+N_H, N_3H = 26, 431
+MOCHY_A, MOCHY_A_PLUS = 1, 2
+OK, W_DEGENERATE_CP = 0, 1
+E_INVALID, E_NOMEM, E_CUDA, E_TIMEOUT, E_NOT_PROJECTED, E_UNSUPPORTED, E_BUSY = \
+    -1, -2, -3, -4, -5, -6, -7
+
+# every symbol declared in include/mochy.h
+EXPORTS = [
+    "mochy_config_default", "mochy_create", "mochy_destroy", "mochy_load", "mochy_load_device",
+    "mochy_get_hypergraph", "mochy_project", "mochy_line_degrees", "mochy_count_exact",
+    "mochy_count_exact_subset", "mochy_count_sampled", "mochy_randomize", "mochy_profile",
+    "mochy_motif_pattern", "mochy_stream", "mochy_device_bytes", "mochy_kernel_launches",
+    "mochy_strerror", "mochy_last_error",
+]
+
+
+class MochyError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: code {code}: {msg}")
+        self.code = code
+
+
+class mochy_config(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("hbm_budget_bytes", ctypes.c_int64), ("device", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmochy.so (built by paper_2310_15668_gb300.build); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise OSError(f"libmochy is not built ({path}); run __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
+            vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+            lib.mochy_strerror.restype = ctypes.c_char_p
+            lib.mochy_strerror.argtypes = [ctypes.c_int]
+            lib.mochy_last_error.restype = ctypes.c_char_p
+            lib.mochy_last_error.argtypes = []
+            lib.mochy_stream.restype = vp
+            lib.mochy_stream.argtypes = [vp]
+            lib.mochy_device_bytes.restype = i64
+            lib.mochy_device_bytes.argtypes = [vp]
+            lib.mochy_kernel_launches.restype = i64
+            lib.mochy_kernel_launches.argtypes = []
+            lib.mochy_config_default.restype = None
+            lib.mochy_config_default.argtypes = [ctypes.POINTER(mochy_config)]
+            lib.mochy_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(mochy_config)]
+            lib.mochy_destroy.argtypes = [vp]
+            lib.mochy_load.argtypes = [vp, i64, i64, vp, vp, vp]
+            lib.mochy_load_device.argtypes = [vp, i64, i64, vp, vp, vp]
+            lib.mochy_get_hypergraph.argtypes = [vp, vp, vp, vp, vp, vp]
+            lib.mochy_project.argtypes = [vp, vp, vp]
+            lib.mochy_line_degrees.argtypes = [vp, vp]
+            lib.mochy_count_exact.argtypes = [vp, vp, vp]
+            lib.mochy_count_exact_subset.argtypes = [vp, vp, i64, vp, vp]
+            lib.mochy_count_sampled.argtypes = [vp, ctypes.c_int, i64, ctypes.c_uint64, vp, vp,
+                                                vp, vp]
+            lib.mochy_randomize.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint32,
+                                            ctypes.POINTER(vp)]
+            lib.mochy_profile.argtypes = [vp, i32, ctypes.c_uint64, vp, vp, vp, vp, vp, vp]
+            lib.mochy_motif_pattern.argtypes = [ctypes.c_int, i32, vp]
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        lib = load_library()
+        raise MochyError(rc, where, lib.mochy_last_error().decode())
+    return rc
+
+
+def mochy_config_default() -> mochy_config:
+    cfg = mochy_config()
+    load_library().mochy_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+def mochy_create(cfg: mochy_config | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().mochy_create(ctypes.byref(h), None if cfg is None else ctypes.byref(cfg)),
+           "mochy_create")
+    return h.value
+
+
+def mochy_destroy(ctx: int) -> None:
+    load_library().mochy_destroy(ctx)
+
+
+def mochy_load(ctx: int, n_nodes: int, offsets: np.ndarray, nodes: np.ndarray) -> int:
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nod = np.ascontiguousarray(nodes, dtype=np.int32)
+    dup = np.zeros(1, np.int64)
+    _check(load_library().mochy_load(ctx, n_nodes, off.size - 1, _p(off),
+                                     _p(nod if nod.size else np.zeros(1, np.int32)), _p(dup)),
+           "mochy_load")
+    return int(dup[0])
+
+
+def mochy_load_device(ctx: int, n_nodes: int, n_edges: int, d_offsets: int, d_nodes: int) -> int:
+    dup = np.zeros(1, np.int64)
+    _check(load_library().mochy_load_device(ctx, n_nodes, n_edges, d_offsets, d_nodes, _p(dup)),
+           "mochy_load_device")
+    return int(dup[0])
+
+
+def mochy_get_hypergraph(ctx: int):
+    lib = load_library()
+    n = np.zeros(3, np.int64)
+    _check(lib.mochy_get_hypergraph(ctx, _p(n[0:1]), _p(n[1:2]), _p(n[2:3]), None, None),
+           "mochy_get_hypergraph")
+    off = np.zeros(int(n[1]) + 1, np.int64)
+    nodes = np.zeros(max(int(n[2]), 1), np.int32)
+    _check(lib.mochy_get_hypergraph(ctx, None, None, None, _p(off), _p(nodes)),
+           "mochy_get_hypergraph")
+    return int(n[0]), off, nodes[:int(n[2])]
+
+
+def mochy_project(ctx: int):
+    nw = np.zeros(1, np.int64)
+    md = np.zeros(1, np.int32)
+    _check(load_library().mochy_project(ctx, _p(nw), _p(md)), "mochy_project")
+    return int(nw[0]), int(md[0])
+
+
+def mochy_line_degrees(ctx: int, n_edges: int) -> np.ndarray:
+    d = np.zeros(max(n_edges, 1), np.int64)
+    _check(load_library().mochy_line_degrees(ctx, _p(d)), "mochy_line_degrees")
+    return d[:n_edges]
+
+
+def mochy_count_exact(ctx: int):
+    h = np.zeros(N_H, np.int64)
+    h3 = np.zeros(N_3H, np.int64)
+    _check(load_library().mochy_count_exact(ctx, _p(h), _p(h3)), "mochy_count_exact")
+    return h, h3
+
+
+def mochy_count_exact_subset(ctx: int, anchors) -> tuple:
+    a = np.ascontiguousarray(anchors, dtype=np.int32)
+    h = np.zeros(N_H, np.int64)
+    h3 = np.zeros(N_3H, np.int64)
+    _check(load_library().mochy_count_exact_subset(ctx, _p(a if a.size else np.zeros(1, np.int32)),
+                                                   a.size, _p(h), _p(h3)),
+           "mochy_count_exact_subset")
+    return h, h3
+
+
+def mochy_count_sampled(ctx: int, method: int, samples: int, seed: int):
+    rh = np.zeros(N_H, np.int64)
+    r3 = np.zeros(N_3H, np.int64)
+    eh = np.zeros(N_H, np.float64)
+    e3 = np.zeros(N_3H, np.float64)
+    _check(load_library().mochy_count_sampled(ctx, method, samples, ctypes.c_uint64(seed), _p(rh),
+                                              _p(r3), _p(eh), _p(e3)), "mochy_count_sampled")
+    return rh, r3, eh, e3
+
+
+def mochy_randomize(ctx: int, seed: int, copy: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().mochy_randomize(ctx, ctypes.c_uint64(seed), ctypes.c_uint32(copy),
+                                          ctypes.byref(h)), "mochy_randomize")
+    return h.value
+
+
+def mochy_profile(ctx: int, n_random: int, seed: int):
+    sig_h = np.zeros(N_H)
+    cp_h = np.zeros(N_H)
+    sig_3h = np.zeros(N_3H)
+    cp_3h = np.zeros(N_3H)
+    ch = np.zeros((1 + n_random, N_H), np.int64)
+    c3 = np.zeros((1 + n_random, N_3H), np.int64)
+    rc = _check(load_library().mochy_profile(ctx, n_random, ctypes.c_uint64(seed), _p(sig_h),
+                                             _p(cp_h), _p(sig_3h), _p(cp_3h), _p(ch), _p(c3)),
+                "mochy_profile")
+    return dict(sig_h=sig_h, cp_h=cp_h, sig_3h=sig_3h, cp_3h=cp_3h, counts_h=ch, counts_3h=c3,
+                degenerate=rc == W_DEGENERATE_CP)
+
+
+def mochy_motif_pattern(kind: int, motif_id: int) -> np.ndarray:
+    out = np.zeros(7, np.uint8)
+    _check(load_library().mochy_motif_pattern(kind, motif_id, _p(out)), "mochy_motif_pattern")
+    return out
+
+
+def mochy_stream(ctx: int) -> int:
+    return load_library().mochy_stream(ctx) or 0
+
+
+def mochy_device_bytes(ctx: int) -> int:
+    return int(load_library().mochy_device_bytes(ctx))
+
+
+def mochy_kernel_launches() -> int:
+    return int(load_library().mochy_kernel_launches())
+
+
+class Context:
+    """Owns one mochy_ctx; `with Context() as c: ...` destroys it on exit."""
+
+    def __init__(self, theta: int = 1, eps: float = 1.0, budget: int = 0, device: int = 0,
+                 stream: int | None = None, handle: int | None = None):
+        if handle is not None:
+            self.h = handle
+        else:
+            cfg = mochy_config_default()
+            cfg.theta, cfg.eps, cfg.hbm_budget_bytes, cfg.device = theta, eps, budget, device
+            cfg.stream = stream
+            self.h = mochy_create(cfg)
+
+    def close(self):
+        if self.h:
+            mochy_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, n_nodes, offsets, nodes):
+        return mochy_load(self.h, n_nodes, offsets, nodes)
+
+    def project(self):
+        return mochy_project(self.h)
+
+    def count_exact(self):
+        return mochy_count_exact(self.h)
+
+    def count_exact_subset(self, anchors):
+        return mochy_count_exact_subset(self.h, anchors)
+
+    def count_sampled(self, method, samples, seed):
+        return mochy_count_sampled(self.h, method, samples, seed)
+
+    def randomize(self, seed, copy):
+        return Context(handle=mochy_randomize(self.h, seed, copy))
+
+    def profile(self, n_random, seed):
+        return mochy_profile(self.h, n_random, seed)
+
+    def hypergraph(self):
+        return mochy_get_hypergraph(self.h)
+
+    def line_degrees(self):
+        n_nodes, off, _ = self.hypergraph()
+        return mochy_line_degrees(self.h, off.size - 1)
+
+    @property
+    def stream(self):
+        return mochy_stream(self.h)

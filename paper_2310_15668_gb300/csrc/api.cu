@@ -1,0 +1,491 @@
+// The C ABI of libmochy (declared in include/mochy.h): contexts, memory
+// accounting and the entry points.  Every computation runs in the kernels of
+// the other files; this file only moves arguments and results.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "common.cuh"
+
+namespace mochy {
+
+static thread_local std::string t_last_error;
+static std::atomic<long long> g_launches{0};
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e),
+           what, file, line);
+  set_error(buf);
+  return e == cudaErrorMemoryAllocation ? MOCHY_E_NOMEM : MOCHY_E_CUDA;
+}
+
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int dev_alloc(mochy_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (ctx->budget > 0 && ctx->held + (int64_t)bytes > ctx->budget)
+    return fail(MOCHY_E_NOMEM, "device memory budget exceeded (" + std::to_string(ctx->held) +
+                                   " + " + std::to_string(bytes) + " > " +
+                                   std::to_string(ctx->budget) + " bytes)");
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(MOCHY_E_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  ctx->held += (int64_t)bytes;
+  return MOCHY_OK;
+}
+
+void dev_free(mochy_ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  if (bytes == 0) bytes = 16;
+  ctx->held -= (int64_t)bytes;
+}
+
+int scratch(mochy_ctx* ctx, int slot, size_t bytes, void** p) {
+  Buffer& b = ctx->scratch[slot];
+  if (b.bytes < bytes) {
+    if (b.p) {
+      MOCHY_CUDA(cudaStreamSynchronize(ctx->stream));
+      dev_free(ctx, b.p, b.bytes);
+      b.p = nullptr;
+      b.bytes = 0;
+    }
+    const size_t grow = bytes + bytes / 4 + 4096;
+    MOCHY_TRY(dev_alloc(ctx, &b.p, grow));
+    b.bytes = grow;
+  }
+  *p = b.p;
+  return MOCHY_OK;
+}
+
+static size_t graph_bytes(const mochy_ctx* c, int which) {
+  switch (which) {
+    case 0: return sizeof(int64_t) * (size_t)(c->n_edges + 1);
+    case 1: return sizeof(int32_t) * (size_t)std::max<int64_t>(c->n_inc, 1);
+    case 2: return (size_t)std::max<int64_t>(c->n_edges, 1);
+    case 3: return sizeof(int64_t) * (size_t)(c->n_nodes + 1);
+    case 4: return sizeof(int32_t) * (size_t)std::max<int64_t>(c->n_inc, 1);
+  }
+  return 0;
+}
+
+void release_projection(mochy_ctx* ctx) {
+  const int64_t E = ctx->n_edges;
+  if (ctx->nadj || ctx->noff) cudaStreamSynchronize(ctx->stream);
+  if (ctx->nadj) {
+    int64_t total = 2 * ctx->n_wedges;
+    dev_free(ctx, ctx->nadj, (size_t)std::max<int64_t>(total, 1) * sizeof(uint2));
+  }
+  if (ctx->noff) dev_free(ctx, ctx->noff, sizeof(int64_t) * (size_t)(E + 1));
+  if (ctx->ustart) dev_free(ctx, ctx->ustart, sizeof(int64_t) * (size_t)std::max<int64_t>(E, 1));
+  if (ctx->uprefix) dev_free(ctx, ctx->uprefix, sizeof(int64_t) * (size_t)(E + 1));
+  if (ctx->row_order)
+    dev_free(ctx, ctx->row_order, sizeof(int32_t) * (size_t)std::max<int64_t>(E, 1));
+  ctx->nadj = nullptr;
+  ctx->noff = ctx->ustart = ctx->uprefix = nullptr;
+  ctx->row_order = nullptr;
+  ctx->projected = false;
+  ctx->n_wedges = 0;
+  ctx->max_deg = 0;
+}
+
+void release_graph(mochy_ctx* ctx) {
+  release_projection(ctx);
+  if (ctx->eoff) {
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, ctx->eoff, graph_bytes(ctx, 0));
+    dev_free(ctx, ctx->enode, graph_bytes(ctx, 1));
+    dev_free(ctx, ctx->esize, graph_bytes(ctx, 2));
+    dev_free(ctx, ctx->voff, graph_bytes(ctx, 3));
+    dev_free(ctx, ctx->vedge, graph_bytes(ctx, 4));
+  }
+  ctx->eoff = nullptr;
+  ctx->enode = nullptr;
+  ctx->esize = nullptr;
+  ctx->voff = nullptr;
+  ctx->vedge = nullptr;
+  ctx->n_nodes = ctx->n_edges = ctx->n_inc = 0;
+  ctx->max_size = 0;
+}
+
+bool host_patterns(int kind, int32_t id, uint8_t* out);  // tables.cu
+
+// Results staging: device int64[457] + double[4*457], mirrored in pinned host memory.
+constexpr size_t kResBytes = 8 * 457 * 5 + 64;
+
+static int device_guard(mochy_ctx* ctx) {
+  MOCHY_CUDA(cudaSetDevice(ctx->device));
+  return MOCHY_OK;
+}
+
+}  // namespace mochy
+
+using namespace mochy;
+
+extern "C" {
+
+void mochy_config_default(mochy_config* cfg) {
+  if (!cfg) return;
+  cfg->theta = 1;
+  cfg->eps = 1.0;
+  cfg->hbm_budget_bytes = 0;
+  cfg->device = 0;
+  cfg->stream = nullptr;
+}
+
+int mochy_create(mochy_ctx** out, const mochy_config* cfg_in) {
+  if (!out) return fail(MOCHY_E_INVALID, "null output handle");
+  *out = nullptr;
+  mochy_config cfg;
+  mochy_config_default(&cfg);
+  if (cfg_in) cfg = *cfg_in;
+  if (cfg.theta < 1) return fail(MOCHY_E_INVALID, "theta must be >= 1");
+  if (!(cfg.eps >= 0.0)) return fail(MOCHY_E_INVALID, "eps must be >= 0");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(MOCHY_E_CUDA, "no CUDA device is available");
+  }
+  if (cfg.device < 0 || cfg.device >= ndev) return fail(MOCHY_E_INVALID, "bad device ordinal");
+  mochy_ctx* ctx = new (std::nothrow) mochy_ctx();
+  if (!ctx) return fail(MOCHY_E_NOMEM, "host allocation failed");
+  ctx->device = cfg.device;
+  ctx->theta = cfg.theta;
+  ctx->eps = cfg.eps;
+  ctx->budget = cfg.hbm_budget_bytes;
+  int rc = MOCHY_OK;
+  auto bail = [&](int code) {
+    mochy_destroy(ctx);
+    return code;
+  };
+  if (cudaSetDevice(cfg.device) != cudaSuccess) return bail(fail(MOCHY_E_CUDA, "cudaSetDevice failed"));
+  if (cfg.stream) {
+    ctx->stream = (cudaStream_t)cfg.stream;
+    ctx->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(fail(MOCHY_E_CUDA, "cudaStreamCreate failed"));
+    ctx->own_stream = true;
+  }
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, cfg.device);
+  ctx->num_sms = v;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, cfg.device);
+  ctx->smem_optin = (size_t)v;
+  void* p = nullptr;
+  if ((rc = dev_alloc(ctx, &p, 432 * 8 + 64 + kResBytes)) < 0) return bail(rc);
+  ctx->hist = (unsigned long long*)p;
+  ctx->counters = (int32_t*)((char*)p + 432 * 8);
+  if (cudaMallocHost(&ctx->pinned, kResBytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->pinned = nullptr;
+    return bail(fail(MOCHY_E_NOMEM, "pinned host allocation failed"));
+  }
+  if ((rc = build_tables(ctx)) < 0) return bail(rc);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    return bail(fail(MOCHY_E_CUDA, "table build failed"));
+  *out = ctx;
+  return MOCHY_OK;
+}
+
+int mochy_destroy(mochy_ctx* ctx) {
+  if (!ctx) return MOCHY_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  release_graph(ctx);
+  for (auto& b : ctx->scratch) {
+    if (b.p) dev_free(ctx, b.p, b.bytes);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  if (ctx->hist) cudaFree(ctx->hist);
+  if (ctx->tables.lut3) cudaFree(ctx->tables.lut3);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return MOCHY_OK;
+}
+
+int mochy_load_device(mochy_ctx* ctx, int64_t n_nodes, int64_t n_edges, const int64_t* d_off,
+                      const int32_t* d_nodes, int64_t* n_dup) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  if (n_edges > 0 && (!d_off || !d_nodes)) return fail(MOCHY_E_INVALID, "null array");
+  MOCHY_TRY(device_guard(ctx));
+  return load_graph(ctx, n_nodes, n_edges, d_off, d_nodes, n_dup);
+}
+
+int mochy_load(mochy_ctx* ctx, int64_t n_nodes, int64_t n_edges, const int64_t* h_off,
+               const int32_t* h_nodes, int64_t* n_dup) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  if (n_edges < 0 || n_nodes < 0) return fail(MOCHY_E_INVALID, "negative size");
+  if (n_edges > 0 && (!h_off || !h_nodes)) return fail(MOCHY_E_INVALID, "null array");
+  MOCHY_TRY(device_guard(ctx));
+  if (n_edges == 0) return load_graph(ctx, n_nodes, 0, nullptr, nullptr, n_dup);
+  if (h_off[0] != 0) return fail(MOCHY_E_INVALID, "offsets must start at 0");
+  const int64_t total = h_off[n_edges];
+  if (total < 0 || total > (int64_t)n_edges * MOCHY_MAX_EDGE_SIZE)
+    return fail(MOCHY_E_INVALID, "bad offsets");
+  void* d = nullptr;
+  const size_t bytes = (size_t)(n_edges + 1) * 8 + (size_t)std::max<int64_t>(total, 1) * 4 + 256;
+  MOCHY_TRY(dev_alloc(ctx, &d, bytes));
+  int64_t* d_off = (int64_t*)d;
+  int32_t* d_nodes = (int32_t*)((char*)d + (((size_t)(n_edges + 1) * 8 + 255) & ~(size_t)255));
+  int rc = MOCHY_OK;
+  cudaError_t e1 = cudaMemcpyAsync(d_off, h_off, (size_t)(n_edges + 1) * 8,
+                                   cudaMemcpyHostToDevice, ctx->stream);
+  cudaError_t e2 = total > 0 ? cudaMemcpyAsync(d_nodes, h_nodes, (size_t)total * 4,
+                                               cudaMemcpyHostToDevice, ctx->stream)
+                             : cudaSuccess;
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    rc = cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaMemcpyAsync", __FILE__, __LINE__);
+  } else {
+    rc = load_graph(ctx, n_nodes, n_edges, d_off, d_nodes, n_dup);
+  }
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(ctx, d, bytes);
+  return rc;
+}
+
+int mochy_get_hypergraph(mochy_ctx* ctx, int64_t* n_nodes, int64_t* n_edges, int64_t* n_inc,
+                         int64_t* h_off, int32_t* h_nodes) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  MOCHY_TRY(device_guard(ctx));
+  if (n_nodes) *n_nodes = ctx->n_nodes;
+  if (n_edges) *n_edges = ctx->n_edges;
+  if (n_inc) *n_inc = ctx->n_inc;
+  if (h_off && ctx->eoff)
+    MOCHY_CUDA(cudaMemcpyAsync(h_off, ctx->eoff, (size_t)(ctx->n_edges + 1) * 8,
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  if (h_nodes && ctx->enode && ctx->n_inc > 0)
+    MOCHY_CUDA(cudaMemcpyAsync(h_nodes, ctx->enode, (size_t)ctx->n_inc * 4,
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  MOCHY_CUDA(cudaStreamSynchronize(ctx->stream));
+  return MOCHY_OK;
+}
+
+int mochy_project(mochy_ctx* ctx, int64_t* n_wedges, int32_t* max_deg) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  if (!ctx->eoff) return fail(MOCHY_E_INVALID, "no hypergraph loaded");
+  MOCHY_TRY(device_guard(ctx));
+  MOCHY_TRY(project_graph(ctx));
+  if (n_wedges) *n_wedges = ctx->n_wedges;
+  if (max_deg) *max_deg = ctx->max_deg;
+  return MOCHY_OK;
+}
+
+int mochy_line_degrees(mochy_ctx* ctx, int64_t* h_deg) {
+  if (!ctx || !h_deg) return fail(MOCHY_E_INVALID, "null argument");
+  if (!ctx->projected) return fail(MOCHY_E_NOT_PROJECTED, "call mochy_project first");
+  MOCHY_TRY(device_guard(ctx));
+  std::vector<int64_t> off((size_t)ctx->n_edges + 1);
+  MOCHY_CUDA(cudaMemcpyAsync(off.data(), ctx->noff, off.size() * 8, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+  MOCHY_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int64_t i = 0; i < ctx->n_edges; ++i) h_deg[i] = off[i + 1] - off[i];
+  return MOCHY_OK;
+}
+
+static int fetch_counts(mochy_ctx* ctx, int64_t* out_h, int64_t* out_3h) {
+  int64_t* d_counts = (int64_t*)((char*)ctx->counters + 64);
+  MOCHY_CUDA(cudaMemsetAsync(ctx->counters + 8, 0, 4, ctx->stream));
+  MOCHY_TRY(finish_counts(ctx, ctx->hist, d_counts, d_counts + MOCHY_N_H));
+  int64_t* h = (int64_t*)ctx->pinned;
+  MOCHY_CUDA(cudaMemcpyAsync(h, d_counts, 457 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  int32_t bad = 0;
+  MOCHY_CUDA(cudaMemcpyAsync(&bad, ctx->counters + 8, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  MOCHY_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (bad) return fail(MOCHY_E_CUDA, "internal error: an instance mapped to no motif");
+  if (out_h) memcpy(out_h, h, MOCHY_N_H * 8);
+  if (out_3h) memcpy(out_3h, h + MOCHY_N_H, MOCHY_N_3H * 8);
+  return MOCHY_OK;
+}
+
+int mochy_count_exact(mochy_ctx* ctx, int64_t* out_h, int64_t* out_3h) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  MOCHY_TRY(device_guard(ctx));
+  MOCHY_TRY(count_exact(ctx, nullptr, 0, ctx->hist));
+  return fetch_counts(ctx, out_h, out_3h);
+}
+
+int mochy_count_exact_subset(mochy_ctx* ctx, const int32_t* h_anchors, int64_t n, int64_t* out_h,
+                             int64_t* out_3h) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  if (n < 0 || (n > 0 && !h_anchors)) return fail(MOCHY_E_INVALID, "bad anchors");
+  if (!ctx->projected) return fail(MOCHY_E_NOT_PROJECTED, "call mochy_project first");
+  MOCHY_TRY(device_guard(ctx));
+  std::vector<char> seen((size_t)ctx->n_edges, 0);
+  for (int64_t a = 0; a < n; ++a) {
+    if (h_anchors[a] < 0 || h_anchors[a] >= ctx->n_edges)
+      return fail(MOCHY_E_INVALID, "anchor out of range");
+    if (seen[(size_t)h_anchors[a]]) return fail(MOCHY_E_INVALID, "repeated anchor");
+    seen[(size_t)h_anchors[a]] = 1;
+  }
+  void* d = nullptr;
+  MOCHY_TRY(dev_alloc(ctx, &d, (size_t)std::max<int64_t>(n, 1) * 4));
+  int rc = MOCHY_OK;
+  if (n > 0 && cudaMemcpyAsync(d, h_anchors, (size_t)n * 4, cudaMemcpyHostToDevice,
+                               ctx->stream) != cudaSuccess) {
+    rc = fail(MOCHY_E_CUDA, "anchor copy failed");
+  }
+  if (rc == MOCHY_OK) rc = count_exact(ctx, (const int32_t*)d, n, ctx->hist);
+  if (rc == MOCHY_OK && n == 0) {
+    cudaMemsetAsync(ctx->hist, 0, 432 * 8, ctx->stream);
+  }
+  if (rc == MOCHY_OK) rc = fetch_counts(ctx, out_h, out_3h);
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(ctx, d, (size_t)std::max<int64_t>(n, 1) * 4);
+  return rc;
+}
+
+int mochy_count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t seed,
+                        int64_t* raw_h, int64_t* raw_3h, double* est_h, double* est_3h) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  MOCHY_TRY(device_guard(ctx));
+  MOCHY_TRY(count_sampled(ctx, method, samples, seed, ctx->hist));
+  int64_t* d_counts = (int64_t*)((char*)ctx->counters + 64);
+  double* d_est = (double*)(d_counts + 457);
+  MOCHY_CUDA(cudaMemsetAsync(ctx->counters + 8, 0, 4, ctx->stream));
+  MOCHY_TRY(finish_counts(ctx, ctx->hist, d_counts, d_counts + MOCHY_N_H));
+  const double numer = method == MOCHY_A ? (double)ctx->n_edges : (double)ctx->n_wedges;
+  MOCHY_TRY(scale_estimates(ctx, d_counts, d_counts + MOCHY_N_H, method, numer, samples, d_est,
+                            d_est + MOCHY_N_H));
+  int64_t* h = (int64_t*)ctx->pinned;
+  MOCHY_CUDA(cudaMemcpyAsync(h, d_counts, 457 * 16, cudaMemcpyDeviceToHost, ctx->stream));
+  MOCHY_CUDA(cudaStreamSynchronize(ctx->stream));
+  const double* he = (const double*)(h + 457);
+  if (raw_h) memcpy(raw_h, h, MOCHY_N_H * 8);
+  if (raw_3h) memcpy(raw_3h, h + MOCHY_N_H, MOCHY_N_3H * 8);
+  if (est_h) memcpy(est_h, he, MOCHY_N_H * 8);
+  if (est_3h) memcpy(est_3h, he + MOCHY_N_H, MOCHY_N_3H * 8);
+  return MOCHY_OK;
+}
+
+static int new_like(mochy_ctx* src, mochy_ctx** out) {
+  mochy_config cfg;
+  mochy_config_default(&cfg);
+  cfg.theta = src->theta;
+  cfg.eps = src->eps;
+  cfg.device = src->device;
+  cfg.hbm_budget_bytes = src->budget;
+  cfg.stream = src->own_stream ? nullptr : (void*)src->stream;
+  return mochy_create(out, &cfg);
+}
+
+int mochy_randomize(mochy_ctx* src, uint64_t seed, uint32_t copy, mochy_ctx** out) {
+  if (!src || !out) return fail(MOCHY_E_INVALID, "null argument");
+  if (!src->eoff) return fail(MOCHY_E_INVALID, "no hypergraph loaded");
+  *out = nullptr;
+  MOCHY_TRY(device_guard(src));
+  mochy_ctx* dst = nullptr;
+  MOCHY_TRY(new_like(src, &dst));
+  int rc = randomize_graph(src, seed, copy, dst);
+  if (rc < 0) {
+    mochy_destroy(dst);
+    return rc;
+  }
+  *out = dst;
+  return MOCHY_OK;
+}
+
+int mochy_profile(mochy_ctx* ctx, int32_t n_random, uint64_t seed, double* sig_h, double* cp_h,
+                  double* sig_3h, double* cp_3h, int64_t* counts_h, int64_t* counts_3h) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  if (n_random <= 0) return fail(MOCHY_E_INVALID, "n_random must be positive");
+  if (!ctx->eoff) return fail(MOCHY_E_INVALID, "no hypergraph loaded");
+  MOCHY_TRY(device_guard(ctx));
+  if (!ctx->projected) MOCHY_TRY(project_graph(ctx));
+  const size_t rows = (size_t)n_random + 1;
+  void* d = nullptr;
+  const size_t bytes = rows * 457 * 8 + 457 * 16 + 64;
+  MOCHY_TRY(dev_alloc(ctx, &d, bytes));
+  int64_t* ch = (int64_t*)d;
+  int64_t* c3 = ch + rows * MOCHY_N_H;
+  double* out = (double*)(c3 + rows * MOCHY_N_3H);
+  int32_t* degen = (int32_t*)(out + 2 * 457);
+  int rc = count_exact(ctx, nullptr, 0, ctx->hist);
+  if (rc == MOCHY_OK) rc = finish_counts(ctx, ctx->hist, ch, c3);
+  mochy_ctx* copy_ctx = nullptr;
+  if (rc == MOCHY_OK) rc = new_like(ctx, &copy_ctx);
+  for (int32_t c = 0; rc == MOCHY_OK && c < n_random; ++c) {
+    rc = randomize_graph(ctx, seed, (uint32_t)c, copy_ctx);
+    if (rc == MOCHY_OK) rc = project_graph(copy_ctx);
+    if (rc == MOCHY_OK) rc = count_exact(copy_ctx, nullptr, 0, copy_ctx->hist);
+    if (rc == MOCHY_OK)
+      rc = finish_counts(copy_ctx, copy_ctx->hist, ch + (size_t)(c + 1) * MOCHY_N_H,
+                         c3 + (size_t)(c + 1) * MOCHY_N_3H);
+    if (rc == MOCHY_OK && cudaStreamSynchronize(copy_ctx->stream) != cudaSuccess)
+      rc = fail(MOCHY_E_CUDA, "copy count failed");
+  }
+  if (copy_ctx) mochy_destroy(copy_ctx);
+  if (rc == MOCHY_OK) rc = significance_cp(ctx, ch, c3, n_random, ctx->eps, out, degen);
+  int32_t hdeg[2] = {0, 0};
+  if (rc == MOCHY_OK) {
+    std::vector<double> hout(2 * 457);
+    if (cudaMemcpyAsync(hout.data(), out, 2 * 457 * 8, cudaMemcpyDeviceToHost, ctx->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(hdeg, degen, 8, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) {
+      rc = fail(MOCHY_E_CUDA, "result copy failed");
+    }
+    if (rc == MOCHY_OK && counts_h)
+      cudaMemcpyAsync(counts_h, ch, rows * MOCHY_N_H * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (rc == MOCHY_OK && counts_3h)
+      cudaMemcpyAsync(counts_3h, c3, rows * MOCHY_N_3H * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = fail(MOCHY_E_CUDA, "sync failed");
+    if (rc == MOCHY_OK) {
+      if (sig_h) memcpy(sig_h, hout.data(), MOCHY_N_H * 8);
+      if (cp_h) memcpy(cp_h, hout.data() + MOCHY_N_H, MOCHY_N_H * 8);
+      if (sig_3h) memcpy(sig_3h, hout.data() + 2 * MOCHY_N_H, MOCHY_N_3H * 8);
+      if (cp_3h) memcpy(cp_3h, hout.data() + 2 * MOCHY_N_H + MOCHY_N_3H, MOCHY_N_3H * 8);
+    }
+  }
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(ctx, d, bytes);
+  if (rc < 0) return rc;
+  return (hdeg[0] || hdeg[1]) ? MOCHY_W_DEGENERATE_CP : MOCHY_OK;
+}
+
+int mochy_motif_pattern(int kind, int32_t id, uint8_t* regions_out) {
+  if (!regions_out) return fail(MOCHY_E_INVALID, "null output");
+  if (!host_patterns(kind, id, regions_out))
+    return fail(MOCHY_E_INVALID, "unknown motif id, or no context created yet");
+  return MOCHY_OK;
+}
+
+void* mochy_stream(mochy_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+int64_t mochy_device_bytes(mochy_ctx* ctx) { return ctx ? ctx->held : 0; }
+
+int64_t mochy_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+const char* mochy_strerror(int code) {
+  switch (code) {
+    case MOCHY_OK: return "ok";
+    case MOCHY_W_DEGENERATE_CP: return "all significances are zero; the CP is zero";
+    case MOCHY_E_INVALID: return "invalid argument or hypergraph";
+    case MOCHY_E_NOMEM: return "out of device memory or over the memory budget";
+    case MOCHY_E_CUDA: return "CUDA error";
+    case MOCHY_E_TIMEOUT: return "a bounded device wait ran out";
+    case MOCHY_E_NOT_PROJECTED: return "the line graph is not built (call mochy_project)";
+    case MOCHY_E_UNSUPPORTED: return "outside the supported limits";
+    case MOCHY_E_BUSY: return "queue full";
+  }
+  return "unknown error";
+}
+
+const char* mochy_last_error(void) { return t_last_error.c_str(); }
+
+}  // extern "C"

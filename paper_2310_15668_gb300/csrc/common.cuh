@@ -1,0 +1,181 @@
+// Internal declarations shared by the libmochy CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/mochy.h"
+
+namespace mochy {
+
+// ---------------------------------------------------------------------------
+// Error handling: every CUDA call is checked; the first failure is recorded
+// in a thread-local message and turned into a MOCHY_E_* return code.
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define MOCHY_CUDA(call)                                                    \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess) return ::mochy::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define MOCHY_TRY(call)          \
+  do {                           \
+    int rc_ = (call);            \
+    if (rc_ < 0) return rc_;     \
+  } while (0)
+
+// Kernel launch bookkeeping (the count is exported for accounting).
+void note_launch(int n = 1);
+#define MOCHY_LAUNCHED() \
+  do { ::mochy::note_launch(); MOCHY_CUDA(cudaGetLastError()); } while (0)
+
+// ---------------------------------------------------------------------------
+// Line-graph entry layout (8 bytes, rows sorted by neighbour id):
+//   w0 bits  0..25  neighbour hyperedge id k
+//   w0 bits 26..31  |e_k| (1..63)
+//   w1              for a row e_i with |e_i| <= 32: bit p set when the p-th
+//                   node of e_i (ascending) lies in e_k, so omega = popc(w1);
+//                   for |e_i| > 32: omega itself.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kIdBits = 26;
+constexpr uint32_t kIdMask = (1u << kIdBits) - 1u;
+constexpr int kMaskedMax = 32;
+
+__host__ __device__ inline uint32_t ent_id(uint2 e) { return e.x & kIdMask; }
+__host__ __device__ inline int ent_size(uint2 e) { return (int)(e.x >> kIdBits); }
+
+// Motif tables on the device.
+struct Tables {
+  uint16_t* lut3 = nullptr;   // [2187] ternary region code -> 3h id (0 invalid)
+  uint8_t* t2h = nullptr;     // [432] 3h id -> h id
+  uint8_t* hopen = nullptr;   // [27]  h id -> 1 if open
+};
+
+// Scratch arena: grows on demand, freed with the context.
+struct Buffer {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace mochy
+
+struct mochy_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int32_t theta = 1;
+  double eps = 1.0;
+  int64_t budget = 0;
+  int64_t held = 0;          // bytes currently allocated by this context
+  int num_sms = 0;
+  size_t smem_optin = 0;
+
+  mochy::Tables tables;
+
+  // hypergraph (after duplicate removal)
+  int64_t n_nodes = 0, n_edges = 0, n_inc = 0;
+  int64_t* eoff = nullptr;     // [E+1]
+  int32_t* enode = nullptr;    // [n_inc] node lists, ascending per hyperedge
+  uint8_t* esize = nullptr;    // [E]
+  int64_t* voff = nullptr;     // [N+1]
+  int32_t* vedge = nullptr;    // [n_inc] incidence lists E_v, ascending
+  int max_size = 0;
+
+  // line graph
+  bool projected = false;
+  int64_t n_wedges = 0;
+  int32_t max_deg = 0;
+  int64_t* noff = nullptr;     // [E+1]
+  uint2* nadj = nullptr;       // [2 |wedges|]
+  int64_t* ustart = nullptr;   // [E]   first entry of row i with k > i
+  int64_t* uprefix = nullptr;  // [E+1] exclusive prefix of upper-row lengths
+  int32_t* row_order = nullptr;  // [E] rows by decreasing estimated work
+
+  // per-call device scratch
+  unsigned long long* hist = nullptr;  // [432] 3h histogram (index = id)
+  int32_t* counters = nullptr;         // [16] work-queue counters / flags
+  mochy::Buffer scratch[4];
+
+  // pinned host staging
+  void* pinned = nullptr;
+};
+
+namespace mochy {
+
+// Memory (budget-checked, tracked per context).
+int dev_alloc(mochy_ctx* ctx, void** p, size_t bytes);
+void dev_free(mochy_ctx* ctx, void* p, size_t bytes);
+int scratch(mochy_ctx* ctx, int slot, size_t bytes, void** p);
+void release_graph(mochy_ctx* ctx);
+void release_projection(mochy_ctx* ctx);
+
+// Primitives (primitives.cu).
+int scan_exclusive_i64(mochy_ctx* ctx, const int64_t* d_in, int64_t* d_out, int64_t n);
+int radix_sort_pairs_u32(mochy_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n,
+                         int key_bits);
+
+// Stages.
+int build_tables(mochy_ctx* ctx);                                     // tables.cu
+int load_graph(mochy_ctx* ctx, int64_t n_nodes, int64_t n_edges,
+               const int64_t* d_off, const int32_t* d_nodes, int64_t* n_dup);  // load.cu
+int project_graph(mochy_ctx* ctx);                                    // project.cu
+int count_exact(mochy_ctx* ctx, const int32_t* d_anchors, int64_t n_anchors,
+                unsigned long long* d_hist);                          // count_exact.cu
+int count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t seed,
+                  unsigned long long* d_hist);                        // sample.cu
+int randomize_graph(mochy_ctx* src, uint64_t seed, uint32_t copy, mochy_ctx* dst);  // nullmodel.cu
+int finish_counts(mochy_ctx* ctx, const unsigned long long* d_hist, int64_t* d_out_h,
+                  int64_t* d_out_3h);                                 // profile.cu
+int scale_estimates(mochy_ctx* ctx, const int64_t* d_raw_h, const int64_t* d_raw_3h,
+                    int method, double numer, int64_t samples, double* d_est_h,
+                    double* d_est_3h);                                // profile.cu
+int significance_cp(mochy_ctx* ctx, const int64_t* d_counts_h, const int64_t* d_counts_3h,
+                    int32_t n_random, double eps, double* d_out /* 4 vectors */,
+                    int32_t* d_degenerate);                           // profile.cu
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Small device helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t warp_incl_scan_i64(int64_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int64_t o = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += o;
+  }
+  return v;
+}
+
+// Exclusive scan across the block of one value per thread; `ws` is shared
+// scratch of 34 int64.  Ends with a barrier, so `ws` can be reused at once.
+__device__ __forceinline__ int64_t block_scan_i64(int64_t v, int64_t* ws, int64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t inc = warp_incl_scan_i64(v);
+  if (lane == 31) ws[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    const int64_t s = lane < nw ? ws[lane] : 0;
+    const int64_t si = warp_incl_scan_i64(s);
+    __syncwarp();
+    ws[lane] = si - s;
+    if (lane == 31) ws[32] = si;
+  }
+  __syncthreads();
+  const int64_t res = ws[warp] + inc - v;
+  *total = ws[32];
+  __syncthreads();
+  return res;
+}
+
+}  // namespace mochy
