@@ -237,8 +237,9 @@ int mochy_load(mochy_ctx* ctx, int64_t n_nodes, int64_t n_edges, const int64_t* 
   if (n_edges == 0) return load_graph(ctx, n_nodes, 0, nullptr, nullptr, n_dup);
   if (h_off[0] != 0) return fail(MOCHY_E_INVALID, "offsets must start at 0");
   const int64_t total = h_off[n_edges];
-  if (total < 0 || total > (int64_t)n_edges * MOCHY_MAX_EDGE_SIZE)
-    return fail(MOCHY_E_INVALID, "bad offsets");
+  if (total < 0) return fail(MOCHY_E_INVALID, "bad offsets");
+  if (total > (int64_t)n_edges * MOCHY_MAX_EDGE_SIZE)
+    return fail(MOCHY_E_UNSUPPORTED, "hyperedge with more than 63 nodes");
   void* d = nullptr;
   const size_t bytes = (size_t)(n_edges + 1) * 8 + (size_t)std::max<int64_t>(total, 1) * 4 + 256;
   MOCHY_TRY(dev_alloc(ctx, &d, bytes));

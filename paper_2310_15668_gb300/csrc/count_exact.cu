@@ -210,16 +210,11 @@ int count_exact(mochy_ctx* ctx, const int32_t* d_anchors, int64_t n_anchors,
     return MOCHY_OK;
   }
   const size_t smem = exact_smem_bytes(ctx->n_edges);
-  if (smem > ctx->smem_optin)
+  // leave room for the kernel's static shared memory
+  if (smem + 1024 > ctx->smem_optin)
     return fail(MOCHY_E_UNSUPPORTED, "exact counting supports at most 786432 hyperedges");
-  static thread_local int configured_dev = -1;
-  static thread_local size_t configured_smem = 0;
-  if (configured_dev != ctx->device || configured_smem < smem) {
-    MOCHY_CUDA(cudaFuncSetAttribute(k_exact_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)ctx->smem_optin));
-    configured_dev = ctx->device;
-    configured_smem = ctx->smem_optin;
-  }
+  MOCHY_CUDA(cudaFuncSetAttribute(k_exact_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
   int per_sm = 0;
   MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exact_rows, kExactThreads,
                                                            smem));

@@ -142,8 +142,9 @@ int load_graph(mochy_ctx* ctx, int64_t n_nodes, int64_t n_edges, const int64_t* 
   if (n_edges > 0) {
     MOCHY_CUDA(cudaMemcpyAsync(&total, d_off + n_edges, 8, cudaMemcpyDeviceToHost, st));
     MOCHY_CUDA(cudaStreamSynchronize(st));
-    if (total < 0 || total > (int64_t)n_edges * MOCHY_MAX_EDGE_SIZE)
-      return fail(MOCHY_E_INVALID, "bad offsets");
+    if (total < 0) return fail(MOCHY_E_INVALID, "bad offsets");
+    if (total > (int64_t)n_edges * MOCHY_MAX_EDGE_SIZE)
+      return fail(MOCHY_E_UNSUPPORTED, "hyperedge with more than 63 nodes");
   }
   // temporaries in scratch slot 0
   uint64_t tsize = 1;

@@ -43,7 +43,7 @@ __device__ int64_t block_excl_scan(int64_t v, int64_t* total) {
   return res;
 }
 
-__global__ void k_scan_partials(const int64_t* __restrict__ in, int64_t n,
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(const int64_t* __restrict__ in, int64_t n,
                                 int64_t* __restrict__ partial) {
   const int64_t tile = (int64_t)blockIdx.x * kScanTile;
   int64_t s = 0;
@@ -58,7 +58,7 @@ __global__ void k_scan_partials(const int64_t* __restrict__ in, int64_t n,
 }
 
 // One block scans the partial sums in place (exclusive), tile by tile.
-__global__ void k_scan_partials_scan(int64_t* partial, int64_t nb) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials_scan(int64_t* partial, int64_t nb) {
   __shared__ int64_t carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
@@ -75,7 +75,7 @@ __global__ void k_scan_partials_scan(int64_t* partial, int64_t nb) {
   }
 }
 
-__global__ void k_scan_apply(const int64_t* __restrict__ in, int64_t n,
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int64_t* __restrict__ in, int64_t n,
                              const int64_t* __restrict__ partial, int64_t* __restrict__ out) {
   const int64_t tile = (int64_t)blockIdx.x * kScanTile;
   int64_t v[kScanItems];
@@ -105,7 +105,7 @@ constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSortWarps = kSortThreads / 32;
 
-__global__ void k_sort_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
                             int64_t* __restrict__ hist, int nblocks) {
   __shared__ unsigned int cnt[256];
   cnt[threadIdx.x] = 0;
@@ -119,7 +119,7 @@ __global__ void k_sort_hist(const uint32_t* __restrict__ keys, int64_t n, int sh
   hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                int64_t n, int shift, const int64_t* __restrict__ offs,
                                int nblocks) {

@@ -13,7 +13,7 @@
 namespace mochy {
 namespace {
 
-__global__ void k_finish(const unsigned long long* __restrict__ hist, const uint8_t* __restrict__ t2h,
+__global__ void __launch_bounds__(512) k_finish(const unsigned long long* __restrict__ hist, const uint8_t* __restrict__ t2h,
                          int64_t* __restrict__ out_h, int64_t* __restrict__ out_3h,
                          int32_t* __restrict__ bad) {
   __shared__ unsigned long long h[27];
@@ -28,7 +28,7 @@ __global__ void k_finish(const unsigned long long* __restrict__ hist, const uint
   if (threadIdx.x == 0 && hist[0] != 0ull) *bad = 1;   // an instance with no motif id
 }
 
-__global__ void k_scale(const int64_t* __restrict__ raw_h, const int64_t* __restrict__ raw_3h,
+__global__ void __launch_bounds__(512) k_scale(const int64_t* __restrict__ raw_h, const int64_t* __restrict__ raw_3h,
                         const uint8_t* __restrict__ t2h, const uint8_t* __restrict__ hopen,
                         int method, double numer, double samples, double* __restrict__ est_h,
                         double* __restrict__ est_3h) {
@@ -68,7 +68,7 @@ __device__ void sig_cp(const int64_t* __restrict__ counts, int n, int R, double 
   __syncthreads();
 }
 
-__global__ void k_sig_cp(const int64_t* __restrict__ counts_h, const int64_t* __restrict__ counts_3h,
+__global__ void __launch_bounds__(256) k_sig_cp(const int64_t* __restrict__ counts_h, const int64_t* __restrict__ counts_3h,
                          int R, double eps, double* __restrict__ out, int32_t* __restrict__ deg) {
   __shared__ double red[1];
   sig_cp(counts_h, MOCHY_N_H, R, eps, out, out + MOCHY_N_H, deg, red);

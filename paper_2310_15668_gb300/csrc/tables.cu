@@ -91,8 +91,8 @@ __device__ int classify_pattern(int code, int base, int* group) {
   return valid ? 1 : 0;
 }
 
-// One block of 1024 threads builds everything.
-__global__ void k_build_tables(uint16_t* lut3, uint8_t* t2h, uint8_t* hopen,
+// One block of 512 threads builds everything.
+__global__ void __launch_bounds__(512) k_build_tables(uint16_t* lut3, uint8_t* t2h, uint8_t* hopen,
                                uint8_t* pat2, uint8_t* pat3) {
   __shared__ int key2[128], ok2[128], grp2[128], hid2[128];
   __shared__ int key3[2187];
@@ -198,7 +198,7 @@ int build_tables(mochy_ctx* ctx) {
   ctx->tables.hopen = ctx->tables.t2h + 432;
   uint8_t* pat2 = ctx->tables.hopen + 27;
   uint8_t* pat3 = pat2 + 27 * 7;
-  k_build_tables<<<1, 1024, 0, ctx->stream>>>(ctx->tables.lut3, ctx->tables.t2h,
+  k_build_tables<<<1, 512, 0, ctx->stream>>>(ctx->tables.lut3, ctx->tables.t2h,
                                               ctx->tables.hopen, pat2, pat3);
   MOCHY_LAUNCHED();
   if (!g_have_patterns) {
