@@ -63,6 +63,11 @@ typedef struct {
   int64_t hbm_budget_bytes; /* device bytes the context may hold; 0 = no cap */
   int32_t device;           /* CUDA device ordinal; 0 */
   void* stream;             /* cudaStream_t to run on; NULL = own stream */
+  int32_t exact_kernel;     /* mochy_count_exact: 0 = split (open pairs counted
+                               per centre, closed ones enumerated), 1 = plain
+                               per-hyperwedge scan; both give the same counts */
+  int32_t dense_threshold;  /* split kernel: line degree from which a row is
+                               kept as a bitmap; 0 = chosen by the tuner */
 } mochy_config;
 
 /* Fill *cfg with the defaults above. */

@@ -85,6 +85,7 @@ static size_t graph_bytes(const mochy_ctx* c, int which) {
 
 void release_projection(mochy_ctx* ctx) {
   const int64_t E = ctx->n_edges;
+  release_split(ctx);
   if (ctx->nadj || ctx->noff) cudaStreamSynchronize(ctx->stream);
   if (ctx->nadj) {
     int64_t total = 2 * ctx->n_wedges;
@@ -127,6 +128,15 @@ bool host_patterns(int kind, int32_t id, uint8_t* out);  // tables.cu
 // Results staging: device int64[457] + double[4*457], mirrored in pinned host memory.
 constexpr size_t kResBytes = 8 * 457 * 5 + 64;
 
+// The exact count through the kernel the configuration selects.
+static int exact_dispatch(mochy_ctx* ctx, unsigned long long* d_hist) {
+  if (!ctx->projected) return fail(MOCHY_E_NOT_PROJECTED, "call mochy_project first");
+  if (ctx->exact_kernel == 1) return count_exact(ctx, nullptr, 0, d_hist);
+  MOCHY_CUDA(cudaMemsetAsync(d_hist, 0, 432 * 8, ctx->stream));
+  if (ctx->n_edges == 0) return MOCHY_OK;
+  return count_exact_split(ctx, d_hist);
+}
+
 static int device_guard(mochy_ctx* ctx) {
   MOCHY_CUDA(cudaSetDevice(ctx->device));
   return MOCHY_OK;
@@ -145,6 +155,8 @@ void mochy_config_default(mochy_config* cfg) {
   cfg->hbm_budget_bytes = 0;
   cfg->device = 0;
   cfg->stream = nullptr;
+  cfg->exact_kernel = 0;
+  cfg->dense_threshold = 0;
 }
 
 int mochy_create(mochy_ctx** out, const mochy_config* cfg_in) {
@@ -155,6 +167,8 @@ int mochy_create(mochy_ctx** out, const mochy_config* cfg_in) {
   if (cfg_in) cfg = *cfg_in;
   if (cfg.theta < 1) return fail(MOCHY_E_INVALID, "theta must be >= 1");
   if (!(cfg.eps >= 0.0)) return fail(MOCHY_E_INVALID, "eps must be >= 0");
+  if (cfg.exact_kernel < 0 || cfg.exact_kernel > 1) return fail(MOCHY_E_INVALID, "bad exact_kernel");
+  if (cfg.dense_threshold < 0) return fail(MOCHY_E_INVALID, "bad dense_threshold");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -167,6 +181,8 @@ int mochy_create(mochy_ctx** out, const mochy_config* cfg_in) {
   ctx->theta = cfg.theta;
   ctx->eps = cfg.eps;
   ctx->budget = cfg.hbm_budget_bytes;
+  ctx->exact_kernel = cfg.exact_kernel;
+  ctx->dense_thr = cfg.dense_threshold;
   int rc = MOCHY_OK;
   auto bail = [&](int code) {
     mochy_destroy(ctx);
@@ -318,7 +334,7 @@ static int fetch_counts(mochy_ctx* ctx, int64_t* out_h, int64_t* out_3h) {
 int mochy_count_exact(mochy_ctx* ctx, int64_t* out_h, int64_t* out_3h) {
   if (!ctx) return fail(MOCHY_E_INVALID, "null context");
   MOCHY_TRY(device_guard(ctx));
-  MOCHY_TRY(count_exact(ctx, nullptr, 0, ctx->hist));
+  MOCHY_TRY(exact_dispatch(ctx, ctx->hist));
   return fetch_counts(ctx, out_h, out_3h);
 }
 
@@ -383,6 +399,8 @@ static int new_like(mochy_ctx* src, mochy_ctx** out) {
   cfg.device = src->device;
   cfg.hbm_budget_bytes = src->budget;
   cfg.stream = src->own_stream ? nullptr : (void*)src->stream;
+  cfg.exact_kernel = src->exact_kernel;
+  cfg.dense_threshold = src->dense_thr;
   return mochy_create(out, &cfg);
 }
 
@@ -417,14 +435,14 @@ int mochy_profile(mochy_ctx* ctx, int32_t n_random, uint64_t seed, double* sig_h
   int64_t* c3 = ch + rows * MOCHY_N_H;
   double* out = (double*)(c3 + rows * MOCHY_N_3H);
   int32_t* degen = (int32_t*)(out + 2 * 457);
-  int rc = count_exact(ctx, nullptr, 0, ctx->hist);
+  int rc = exact_dispatch(ctx, ctx->hist);
   if (rc == MOCHY_OK) rc = finish_counts(ctx, ctx->hist, ch, c3);
   mochy_ctx* copy_ctx = nullptr;
   if (rc == MOCHY_OK) rc = new_like(ctx, &copy_ctx);
   for (int32_t c = 0; rc == MOCHY_OK && c < n_random; ++c) {
     rc = randomize_graph(ctx, seed, (uint32_t)c, copy_ctx);
     if (rc == MOCHY_OK) rc = project_graph(copy_ctx);
-    if (rc == MOCHY_OK) rc = count_exact(copy_ctx, nullptr, 0, copy_ctx->hist);
+    if (rc == MOCHY_OK) rc = exact_dispatch(copy_ctx, copy_ctx->hist);
     if (rc == MOCHY_OK)
       rc = finish_counts(copy_ctx, copy_ctx->hist, ch + (size_t)(c + 1) * MOCHY_N_H,
                          c3 + (size_t)(c + 1) * MOCHY_N_3H);

@@ -99,6 +99,27 @@ struct mochy_ctx {
   int64_t* uprefix = nullptr;  // [E+1] exclusive prefix of upper-row lengths
   int32_t* row_order = nullptr;  // [E] rows by decreasing estimated work
 
+  // exact count, split path (built on first use, released with the line graph):
+  // rows of line degree >= dense_thr are "dense" and get bitmaps over the
+  // dense-row index space; nodes with >= heavy_thr dense hyperedges get one too.
+  int exact_kernel = 0;          // 0 split (default), 1 wedge-scan
+  int32_t dense_thr = 0;         // 0 = chosen by the tuner
+  int32_t heavy_thr = 32;
+  bool split_ready = false;
+  int64_t n_dense = 0, n_sparse = 0, n_heavy = 0, wwords = 0;
+  int32_t* dense_idx = nullptr;   // [E]  dense index or -1
+  int32_t* dense_row = nullptr;   // [n_dense]
+  uint32_t* dbits = nullptr;      // [n_dense][2][wwords]  adjacency, omega >= 2
+  int32_t* heavy_idx = nullptr;   // [N]  heavy index or -1
+  uint32_t* nbits = nullptr;      // [n_heavy][wwords]  dense members of E_v
+  uint32_t* sbits = nullptr;      // [5][wwords]  size class of dense rows
+  int32_t* dense_order = nullptr;   // dense rows by decreasing work
+  int32_t* sparse_order = nullptr;  // sparse rows by decreasing work
+  int64_t* dvoff = nullptr;         // [N+1] dense members of E_v ...
+  int32_t* dvedge = nullptr;        // ... as dense indices, ascending
+  size_t split_bytes = 0, nbits_bytes = 0, dinc_bytes = 0;
+  int32_t dense_thr_used = 0;
+
   // per-call device scratch
   unsigned long long* hist = nullptr;  // [432] 3h histogram (index = id)
   int32_t* counters = nullptr;         // [16] work-queue counters / flags
@@ -129,6 +150,9 @@ int load_graph(mochy_ctx* ctx, int64_t n_nodes, int64_t n_edges,
 int project_graph(mochy_ctx* ctx);                                    // project.cu
 int count_exact(mochy_ctx* ctx, const int32_t* d_anchors, int64_t n_anchors,
                 unsigned long long* d_hist);                          // count_exact.cu
+int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist);    // count_split.cu
+int prepare_split(mochy_ctx* ctx);                                    // count_split.cu
+void release_split(mochy_ctx* ctx);                                   // count_split.cu
 int count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t seed,
                   unsigned long long* d_hist);                        // sample.cu
 int randomize_graph(mochy_ctx* src, uint64_t seed, uint32_t copy, mochy_ctx* dst);  // nullmodel.cu

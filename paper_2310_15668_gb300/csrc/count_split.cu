@@ -1,0 +1,841 @@
+// Exact counting (MoCHy-E, Algorithm "exact_motif_counting", Section 3.2)
+// split into open and closed instances.
+//
+// Algorithm exact_motif_counting enumerates, for each centre e_c, every pair
+// {e_p, e_q} of its neighbours.  Here the same counts are reached in two
+// parts.
+//
+// Open instances.  For a pair of neighbours that are not adjacent the seven
+// regions (Lemma "motif:time") are |e_c| - w_p - w_q, |e_p| - w_p,
+// |e_q| - w_q, w_p, 0, w_q, 0 (w_x = |e_c & e_x|), so the motif depends only
+// on the class (w_x, min(|e_x| - w_x, theta + 1)) of each leaf.  Per centre,
+// the pairs of all neighbour classes are counted from a class histogram; the
+// pairs that are in fact adjacent (closed triangles through e_c) are then
+// taken out again, one "as if open" term per centre of every triangle.  A pair
+// whose overlaps with e_c exceed |e_c| cannot be open and is skipped on both
+// sides.
+//
+// Closed instances (triangles of the line graph) are enumerated once each,
+// from their smallest member in the order "sparse rows (by id) before dense
+// rows (by id)", where a row is dense when its line degree is at least a
+// threshold.  A triangle of three dense rows is found with bitmaps over the
+// dense rows: 32 candidate third hyperedges per word, and when both overlaps
+// with the candidate are 1 the triple intersection is whether the candidate
+// holds a node of e_a & e_b (node bitmaps), so such candidates are counted by
+// popcount per (triple intersection, size class).  Every other candidate is
+// classified exactly from node lists.  Triangles with a sparse smallest member
+// are enumerated from a staged copy of that member's row.
+#include "classify.cuh"
+
+namespace mochy {
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+constexpr int kOpenThreads = 256;
+constexpr int kOpenWarps = kOpenThreads / 32;
+constexpr int kTable = 256;   // per-warp class table of the open-pair kernel
+constexpr int kClasses = 5;   // size classes of a simple closed candidate
+
+// Size class of |e_k| for a closed candidate with both overlaps 1: its motif
+// and its three "as if open" terms depend on |e_k| only through the states
+// of |e_k| - 1 and |e_k| - 2 and whether |e_k| >= 2.
+__host__ __device__ inline int size_class(int C, int theta) {
+  if (C <= 1) return 0;
+  if (C == 2) return 1;
+  if (C <= theta + 1) return 2;
+  if (C == theta + 2) return 3;
+  return 4;
+}
+
+__device__ inline int class_rep(int c, int theta) {
+  return c == 0 ? 1 : c == 1 ? 2 : c == 2 ? 3 : c == 3 ? theta + 2 : theta + 3;
+}
+
+__device__ __forceinline__ void hadd(unsigned long long* h, int id, long long v) {
+  atomicAdd(&h[id], (unsigned long long)v);
+}
+
+// One closed instance {a, b, k} with sizes A, B, C, omega_ab = x,
+// omega_bk = y, omega_ka = z and triple intersection t, counted n times:
+// its motif, minus its "as if open" term at each centre (see above).
+__device__ __forceinline__ void add_triangle(unsigned long long* hist, const uint16_t* lut, int theta,
+                                             int A, int B, int C, int x, int y, int z, int t,
+                                             long long n) {
+  hadd(hist, lut[ternary_code(A, B, C, x, y, z, t, theta)], n);
+  if (x + z <= A) hadd(hist, lut[ternary_code(A, B, C, x, 0, z, 0, theta)], -n);
+  if (x + y <= B) hadd(hist, lut[ternary_code(B, A, C, x, 0, y, 0, theta)], -n);
+  if (z + y <= C) hadd(hist, lut[ternary_code(C, A, B, z, 0, y, 0, theta)], -n);
+}
+
+// binary search of node u in an ascending list in shared memory
+__device__ __forceinline__ bool has_node(const int32_t* s, int n, int32_t u) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int m = (lo + hi) >> 1;
+    if (s[m] < u) lo = m + 1; else hi = m;
+  }
+  return lo < n && s[lo] == u;
+}
+
+struct SplitArgs {
+  int64_t n_edges;
+  const int64_t* eoff;
+  const int32_t* enode;
+  const int64_t* voff;
+  const int32_t* vedge;
+  const int64_t* noff;
+  const uint2* nadj;
+  const uint16_t* lut3;
+  unsigned long long* hist;
+  int theta;
+  // split structures
+  int64_t n_dense, wwords;
+  const int32_t* dense_idx;
+  const int32_t* dense_row;
+  const uint32_t* dbits;
+  const int32_t* heavy_idx;
+  const uint32_t* nbits;
+  const uint32_t* sbits;
+  const int64_t* dvoff;
+  const int32_t* dvedge;
+  const int32_t* order;
+  int64_t n_order;
+  int32_t* queue;
+};
+
+__device__ __forceinline__ void load_lut(uint16_t* lut, const uint16_t* g, unsigned long long* hist) {
+  for (int q = threadIdx.x; q < 432; q += blockDim.x) hist[q] = 0ull;
+  for (int q = threadIdx.x; q < 2187; q += blockDim.x) lut[q] = g[q];
+}
+
+__device__ __forceinline__ void flush_hist(unsigned long long* g, const unsigned long long* h) {
+  for (int q = threadIdx.x; q < 432; q += blockDim.x)
+    if (h[q]) atomicAdd(&g[q], h[q]);
+}
+
+// ---------------------------------------------------------------------------
+// Open pairs: one warp per centre row.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
+  __shared__ unsigned long long hist[432];
+  __shared__ uint16_t lut[2192];
+  __shared__ int32_t tkey[kOpenWarps][kTable];
+  __shared__ int32_t tcnt[kOpenWarps][kTable];
+  load_lut(lut, g.lut3, hist);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t* key = tkey[warp];
+  int32_t* cnt = tcnt[warp];
+  constexpr int kPer = kTable / 32;
+  const int64_t nw = (int64_t)gridDim.x * kOpenWarps;
+  for (int64_t c = (int64_t)blockIdx.x * kOpenWarps + warp; c < g.n_edges; c += nw) {
+    const int64_t rb = g.noff[c], re = g.noff[c + 1];
+    if (re - rb < 2) continue;
+    const int A = (int)(g.eoff[c + 1] - g.eoff[c]);
+    for (int q = lane; q < kTable; q += 32) { key[q] = -1; cnt[q] = 0; }
+    __syncwarp();
+    bool overflow = false;
+    for (int64_t p = rb + lane; p < re; p += 32) {
+      const uint2 e = g.nadj[p];
+      const int x = entry_omega(e.y, A);
+      const int s = min(ent_size(e) - x, g.theta + 1);
+      const int k = (x << 8) | s;
+      unsigned h = ((unsigned)k * 2654435761u) >> 24;   // 8 bits
+      int probes = 0;
+      while (true) {
+        const int old = atomicCAS(&key[h], -1, k);
+        if (old == -1 || old == k) { atomicAdd(&cnt[h], 1); break; }
+        h = (h + 1) & (kTable - 1);
+        if (++probes >= kTable) { overflow = true; break; }
+      }
+    }
+    overflow = __any_sync(0xffffffffu, overflow);
+    __syncwarp();
+    if (overflow) {
+      // more distinct classes than the table holds: enumerate the pairs
+      for (int64_t p = rb; p < re; ++p) {
+        const uint2 ep = g.nadj[p];
+        const int x1 = entry_omega(ep.y, A);
+        for (int64_t q = p + 1 + lane; q < re; q += 32) {
+          const uint2 eq = g.nadj[q];
+          const int x2 = entry_omega(eq.y, A);
+          if (x1 + x2 > A) continue;
+          hadd(hist, lut[ternary_code(A, ent_size(ep), ent_size(eq), x1, 0, x2, 0, g.theta)], 1);
+        }
+      }
+      __syncwarp();
+      continue;
+    }
+    // compact the used slots to the front, in place (each lane first reads
+    // its kPer consecutive slots)
+    int32_t rk[kPer], rc[kPer];
+    int mine = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      rk[q] = key[lane * kPer + q];
+      rc[q] = cnt[lane * kPer + q];
+      mine += rk[q] != -1 ? 1 : 0;
+    }
+    int incl = mine;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int o = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += o;
+    }
+    const int P = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    int pos = incl - mine;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q)
+      if (rk[q] != -1) { key[pos] = rk[q]; cnt[pos] = rc[q]; ++pos; }
+    __syncwarp();
+    for (int i = lane; i < P; i += 32) {
+      const int x1 = key[i] >> 8, s1 = key[i] & 255;
+      const long long n1 = cnt[i];
+      for (int j = i; j < P; ++j) {
+        const int x2 = key[j] >> 8, s2 = key[j] & 255;
+        if (x1 + x2 > A) continue;
+        const long long n2 = cnt[j];
+        const long long n = i == j ? n1 * (n1 - 1) / 2 : n1 * n2;
+        if (n) hadd(hist, lut[ternary_code(A, x1 + s1, x2 + s2, x1, 0, x2, 0, g.theta)], n);
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  flush_hist(g.hist, hist);
+}
+
+// ---------------------------------------------------------------------------
+// Triangles with three dense rows: CTA per dense row a.
+// Shared layout: hist | lut | anodes[64] | per-warp (bnodes[64], ihv[64],
+// ilv[64], meta[4]) | A1[W] | A2[W]
+// ---------------------------------------------------------------------------
+struct WarpScratch {
+  int32_t bnodes[64];
+  int32_t ihv[64];
+  int32_t ilv[64];
+  int32_t meta[4];
+};
+
+__global__ void __launch_bounds__(kThreads) k_dense_triangles(SplitArgs g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* hist = (unsigned long long*)smem;
+  uint16_t* lut = (uint16_t*)(hist + 432);
+  int32_t* anodes = (int32_t*)(lut + 2192);
+  WarpScratch* ws = (WarpScratch*)(anodes + 64);
+  uint32_t* A1 = (uint32_t*)(ws + kWarps);
+  const int64_t W = g.wwords;
+  uint32_t* A2 = A1 + W;
+  __shared__ int64_t slot_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WarpScratch& me = ws[warp];
+  load_lut(lut, g.lut3, hist);
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) slot_s = atomicAdd(g.queue, 1);
+    __syncthreads();
+    const int64_t slot = slot_s;
+    if (slot >= g.n_order) break;
+    const int64_t a = g.order[slot];
+    const int ad = g.dense_idx[a];
+    const int64_t rb = g.noff[a], re = g.noff[a + 1];
+    const int A = (int)(g.eoff[a + 1] - g.eoff[a]);
+    if (threadIdx.x < A) anodes[threadIdx.x] = g.enode[g.eoff[a] + threadIdx.x];
+    for (int64_t q = threadIdx.x; q < 2 * W; q += kThreads) A1[q] = 0u;
+    __syncthreads();
+    for (int64_t p = rb + threadIdx.x; p < re; p += kThreads) {
+      const uint2 e = g.nadj[p];
+      const int kd = g.dense_idx[ent_id(e)];
+      if (kd < 0) continue;
+      atomicOr(&A1[kd >> 5], 1u << (kd & 31));
+      if (entry_omega(e.y, A) >= 2) atomicOr(&A2[kd >> 5], 1u << (kd & 31));
+    }
+    __syncthreads();
+    for (int64_t idx = rb + warp; idx < re; idx += kWarps) {
+      const uint2 eab = g.nadj[idx];
+      const int64_t b = ent_id(eab);
+      const int bd = g.dense_idx[b];
+      if (bd <= ad) continue;                       // b must be dense and after a
+      const int B = ent_size(eab);
+      const int x = entry_omega(eab.y, A);
+      if (lane < B) me.bnodes[lane] = g.enode[g.eoff[b] + lane];
+      if (B > 32 && lane + 32 < B) me.bnodes[lane + 32] = g.enode[g.eoff[b] + lane + 32];
+      __syncwarp();
+      // e_a & e_b split into heavy nodes (bitmaps) and light nodes (lists)
+      int nh = 0, nl = 0;
+      for (int base = 0; base < B; base += 32) {
+        const int l = base + lane;
+        const int32_t u = l < B ? me.bnodes[l] : -1;
+        const bool common = l < B && has_node(anodes, A, u);
+        const int hv = common ? g.heavy_idx[u] : -1;
+        const unsigned bh = __ballot_sync(0xffffffffu, common && hv >= 0);
+        const unsigned bl = __ballot_sync(0xffffffffu, common && hv < 0);
+        if (common && hv >= 0) me.ihv[nh + __popc(bh & ((1u << lane) - 1u))] = hv;
+        if (common && hv < 0) me.ilv[nl + __popc(bl & ((1u << lane) - 1u))] = u;
+        nh += __popc(bh);
+        nl += __popc(bl);
+      }
+      __syncwarp();
+      const uint32_t* B1 = g.dbits + (int64_t)bd * 2 * W;
+      const uint32_t* B2 = B1 + W;
+      long long c0[kClasses], c1[kClasses];
+#pragma unroll
+      for (int c = 0; c < kClasses; ++c) { c0[c] = 0; c1[c] = 0; }
+      const int64_t first = (int64_t)(bd + 1);
+      const int64_t fw = first >> 5;
+      for (int64_t w = fw + lane; w < W; w += 32) {
+        uint32_t m = A1[w] & __ldg(&B1[w]);
+        if (w == fw) m &= 0xffffffffu << (first & 31);
+        if (!m) continue;
+        const uint32_t ex = m & (A2[w] | __ldg(&B2[w]));
+        const uint32_t simple = m & ~ex;
+        if (simple) {
+          uint32_t T = 0u;
+          for (int h = 0; h < nh; ++h) T |= __ldg(&g.nbits[(int64_t)me.ihv[h] * W + w]);
+          const uint32_t s1 = simple & T, s0 = simple & ~T;
+#pragma unroll
+          for (int c = 0; c < kClasses; ++c) {
+            const uint32_t sc = __ldg(&g.sbits[(int64_t)c * W + w]);
+            c1[c] += __popc(s1 & sc);
+            c0[c] += __popc(s0 & sc);
+          }
+        }
+        uint32_t e = ex;
+        while (e) {
+          const int bit = __ffs(e) - 1;
+          e &= e - 1;
+          const int64_t k = g.dense_row[w * 32 + bit];
+          const int64_t kb = g.eoff[k];
+          const int C = (int)(g.eoff[k + 1] - kb);
+          int y = 0, z = 0, t = 0;
+          for (int q = 0; q < C; ++q) {
+            const int32_t u = g.enode[kb + q];
+            const bool ia = has_node(anodes, A, u), ib = has_node(me.bnodes, B, u);
+            z += ia; y += ib; t += ia && ib;
+          }
+          add_triangle(hist, lut, g.theta, A, B, C, x, y, z, t, 1);
+        }
+      }
+      // candidates through a light node of e_a & e_b: simple ones have t = 1
+      for (int l = 0; l < nl; ++l) {
+        const int32_t v = me.ilv[l];
+        for (int64_t q = g.dvoff[v] + lane; q < g.dvoff[v + 1]; q += 32) {
+          const int kd = g.dvedge[q];
+          if (kd <= bd) continue;
+          const int64_t k = g.dense_row[kd];
+          const int w = kd >> 5;
+          const uint32_t bit = 1u << (kd & 31);
+          if (!(A1[w] & __ldg(&B1[w]) & bit)) continue;
+          if ((A2[w] | __ldg(&B2[w])) & bit) continue;
+          uint32_t T = 0u;
+          for (int h = 0; h < nh; ++h) T |= __ldg(&g.nbits[(int64_t)me.ihv[h] * W + w]);
+          if (T & bit) continue;
+          const int c = size_class((int)(g.eoff[k + 1] - g.eoff[k]), g.theta);
+#pragma unroll
+          for (int cc = 0; cc < kClasses; ++cc)
+            if (cc == c) { c0[cc] -= 1; c1[cc] += 1; }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < kClasses; ++c) {
+        long long v0 = c0[c], v1 = c1[c];
+        for (int d = 16; d; d >>= 1) {
+          v0 += __shfl_xor_sync(0xffffffffu, v0, d);
+          v1 += __shfl_xor_sync(0xffffffffu, v1, d);
+        }
+        if (lane == 0) {
+          const int C = class_rep(c, g.theta);
+          if (v0) add_triangle(hist, lut, g.theta, A, B, C, x, 1, 1, 0, v0);
+          if (v1) add_triangle(hist, lut, g.theta, A, B, C, x, 1, 1, 1, v1);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  flush_hist(g.hist, hist);
+}
+
+// ---------------------------------------------------------------------------
+// Triangles whose smallest member (sparse rows first) is a sparse row a:
+// CTA per sparse row; the row is staged in shared memory.
+// Shared layout: hist | lut | anodes[64] | per-warp bnodes[64] |
+// key[D] | w1[D] | size[D] | didx[D]
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_sparse_triangles(SplitArgs g, int max_deg) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* hist = (unsigned long long*)smem;
+  uint16_t* lut = (uint16_t*)(hist + 432);
+  int32_t* anodes = (int32_t*)(lut + 2192);
+  int32_t* bnodes_all = anodes + 64;
+  uint32_t* skey = (uint32_t*)(bnodes_all + 64 * kWarps);
+  uint32_t* sw1 = skey + max_deg;
+  int32_t* sdi = (int32_t*)(sw1 + max_deg);
+  uint8_t* ssz = (uint8_t*)(sdi + max_deg);
+  __shared__ int64_t slot_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t* bnodes = bnodes_all + 64 * warp;
+  const int64_t W = g.wwords;
+  load_lut(lut, g.lut3, hist);
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) slot_s = atomicAdd(g.queue, 1);
+    __syncthreads();
+    const int64_t slot = slot_s;
+    if (slot >= g.n_order) break;
+    const int64_t a = g.order[slot];
+    const int64_t rb = g.noff[a], re = g.noff[a + 1];
+    const int deg = (int)(re - rb);
+    if (deg < 2) continue;
+    const int A = (int)(g.eoff[a + 1] - g.eoff[a]);
+    if (threadIdx.x < A) anodes[threadIdx.x] = g.enode[g.eoff[a] + threadIdx.x];
+    for (int q = threadIdx.x; q < deg; q += kThreads) {
+      const uint2 e = g.nadj[rb + q];
+      skey[q] = ent_id(e);
+      sw1[q] = e.y;
+      ssz[q] = (uint8_t)ent_size(e);
+      sdi[q] = g.dense_idx[ent_id(e)];
+    }
+    __syncthreads();
+    for (int ib = warp; ib < deg; ib += kWarps) {
+      const int64_t b = skey[ib];
+      const int bd = sdi[ib];
+      if (bd < 0 && b < a) continue;                 // b must come after a
+      const int B = ssz[ib];
+      const uint32_t mab = sw1[ib];
+      const int x = entry_omega(mab, A);
+      if (lane < B) bnodes[lane] = g.enode[g.eoff[b] + lane];
+      if (B > 32 && lane + 32 < B) bnodes[lane + 32] = g.enode[g.eoff[b] + lane + 32];
+      __syncwarp();
+      if (bd >= 0) {
+        // b dense: every k after b is dense with a larger dense index
+        const uint32_t* B1 = g.dbits + (int64_t)bd * 2 * W;
+        const uint32_t* B2 = B1 + W;
+        for (int q = lane; q < deg; q += 32) {
+          const int kd = sdi[q];
+          if (kd <= bd) continue;
+          const uint32_t bit = 1u << (kd & 31);
+          if (!(__ldg(&B1[kd >> 5]) & bit)) continue;
+          const int64_t k = skey[q];
+          const int C = ssz[q];
+          int y = 1;
+          if (__ldg(&B2[kd >> 5]) & bit) {
+            const int64_t kb = g.eoff[k];
+            y = sorted_overlap(bnodes, B, g.enode + kb, C);
+          }
+          const int z = entry_omega(sw1[q], A);
+          int t;
+          if (A <= kMaskedMax) {
+            t = __popc(mab & sw1[q]);
+          } else {
+            t = sorted_overlap3(anodes, A, bnodes, B, g.enode + g.eoff[k], C);
+          }
+          add_triangle(hist, lut, g.theta, A, B, C, x, y, z, t, 1);
+        }
+      } else {
+        // b sparse: k in both rows and after b (dense, or sparse with k > b)
+        const int64_t bb = g.noff[b], be = g.noff[b + 1];
+        for (int64_t p = bb + lane; p < be; p += 32) {
+          const uint2 ebk = g.nadj[p];
+          const int64_t k = ent_id(ebk);
+          if (k == a) continue;
+          int lo = 0, hi = deg;
+          while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if ((int64_t)skey[m] < k) lo = m + 1; else hi = m;
+          }
+          if (lo >= deg || (int64_t)skey[lo] != k) continue;
+          if (sdi[lo] < 0 && k < b) continue;
+          const int C = ent_size(ebk);
+          const int y = entry_omega(ebk.y, B);
+          const int z = entry_omega(sw1[lo], A);
+          int t;
+          if (A <= kMaskedMax) {
+            t = __popc(mab & sw1[lo]);
+          } else {
+            t = sorted_overlap3(anodes, A, bnodes, B, g.enode + g.eoff[k], C);
+          }
+          add_triangle(hist, lut, g.theta, A, B, C, x, y, z, t, 1);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  flush_hist(g.hist, hist);
+}
+
+// ---------------------------------------------------------------------------
+// Preparation kernels.
+// ---------------------------------------------------------------------------
+__global__ void k_dense_flags(int64_t E, const int64_t* __restrict__ noff, int32_t thr,
+                              int64_t* __restrict__ flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < E) flag[i] = (noff[i + 1] - noff[i]) >= thr ? 1 : 0;
+  if (i == E) flag[i] = 0;
+}
+
+__global__ void k_dense_index(int64_t E, const int64_t* __restrict__ flag,
+                              const int64_t* __restrict__ pos, int32_t* __restrict__ didx,
+                              int32_t* __restrict__ drow) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  if (flag[i]) {
+    didx[i] = (int32_t)pos[i];
+    drow[pos[i]] = (int32_t)i;
+  } else {
+    didx[i] = -1;
+  }
+}
+
+__global__ void k_dense_bits(int64_t n_dense, int64_t W, const int32_t* __restrict__ drow,
+                             const int64_t* __restrict__ eoff, const int64_t* __restrict__ noff,
+                             const uint2* __restrict__ nadj, const int32_t* __restrict__ didx,
+                             uint32_t* __restrict__ dbits) {
+  for (int64_t r = blockIdx.x; r < n_dense; r += gridDim.x) {
+    const int64_t b = drow[r];
+    const int B = (int)(eoff[b + 1] - eoff[b]);
+    uint32_t* B1 = dbits + r * 2 * W;
+    uint32_t* B2 = B1 + W;
+    for (int64_t p = noff[b] + threadIdx.x; p < noff[b + 1]; p += blockDim.x) {
+      const uint2 e = nadj[p];
+      const int kd = didx[ent_id(e)];
+      if (kd < 0) continue;
+      atomicOr(&B1[kd >> 5], 1u << (kd & 31));
+      if (entry_omega(e.y, B) >= 2) atomicOr(&B2[kd >> 5], 1u << (kd & 31));
+    }
+  }
+}
+
+__global__ void k_heavy_flags(int64_t N, const int64_t* __restrict__ voff,
+                              const int32_t* __restrict__ vedge, const int32_t* __restrict__ didx,
+                              int32_t thr, int64_t* __restrict__ flag) {
+  const int64_t v = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (v > N) return;
+  if (v == N) { if (lane == 0) flag[v] = 0; return; }
+  int c = 0;
+  for (int64_t q = voff[v] + lane; q < voff[v + 1]; q += 32) c += didx[vedge[q]] >= 0 ? 1 : 0;
+  for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+  if (lane == 0) flag[v] = c >= thr ? 1 : 0;
+}
+
+__global__ void k_heavy_index(int64_t N, const int64_t* __restrict__ flag,
+                              const int64_t* __restrict__ pos, int32_t* __restrict__ hidx) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < N) hidx[v] = flag[v] ? (int32_t)pos[v] : -1;
+}
+
+__global__ void k_heavy_bits(int64_t N, int64_t W, const int64_t* __restrict__ voff,
+                             const int32_t* __restrict__ vedge, const int32_t* __restrict__ didx,
+                             const int32_t* __restrict__ hidx, uint32_t* __restrict__ nbits) {
+  const int64_t v = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (v >= N) return;
+  const int h = hidx[v];
+  if (h < 0) return;
+  uint32_t* bits = nbits + (int64_t)h * W;
+  for (int64_t q = voff[v] + lane; q < voff[v + 1]; q += 32) {
+    const int kd = didx[vedge[q]];
+    if (kd >= 0) atomicOr(&bits[kd >> 5], 1u << (kd & 31));
+  }
+}
+
+// dense members of each E_v, as ascending dense indices (one warp per node)
+__global__ void k_dense_count(int64_t N, const int64_t* __restrict__ voff,
+                              const int32_t* __restrict__ vedge, const int32_t* __restrict__ didx,
+                              int64_t* __restrict__ cnt) {
+  const int64_t v = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (v > N) return;
+  if (v == N) { if (lane == 0) cnt[v] = 0; return; }
+  int c = 0;
+  for (int64_t q = voff[v] + lane; q < voff[v + 1]; q += 32) c += didx[vedge[q]] >= 0 ? 1 : 0;
+  for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+  if (lane == 0) cnt[v] = c;
+}
+
+__global__ void k_dense_fill(int64_t N, const int64_t* __restrict__ voff,
+                             const int32_t* __restrict__ vedge, const int32_t* __restrict__ didx,
+                             const int64_t* __restrict__ dvoff, int32_t* __restrict__ dvedge) {
+  const int64_t v = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (v >= N) return;
+  int64_t o = dvoff[v];
+  for (int64_t q0 = voff[v]; q0 < voff[v + 1]; q0 += 32) {
+    const int64_t q = q0 + lane;
+    const int kd = q < voff[v + 1] ? didx[vedge[q]] : -1;
+    const unsigned bal = __ballot_sync(0xffffffffu, kd >= 0);
+    if (kd >= 0) dvedge[o + __popc(bal & ((1u << lane) - 1u))] = kd;
+    o += __popc(bal);
+  }
+}
+
+__global__ void k_size_bits(int64_t n_dense, int64_t W, const int32_t* __restrict__ drow,
+                            const int64_t* __restrict__ eoff, int theta, uint32_t* __restrict__ sbits) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_dense) return;
+  const int64_t k = drow[r];
+  const int c = size_class((int)(eoff[k + 1] - eoff[k]), theta);
+  atomicOr(&sbits[(int64_t)c * W + (r >> 5)], 1u << (r & 31));
+}
+
+// stable split of row_order into dense and sparse work orders
+__global__ void k_split_flags(int64_t E, const int32_t* __restrict__ order,
+                              const int32_t* __restrict__ didx, int64_t* __restrict__ fd,
+                              int64_t* __restrict__ fs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > E) return;
+  if (i == E) { fd[i] = 0; fs[i] = 0; return; }
+  const bool d = didx[order[i]] >= 0;
+  fd[i] = d ? 1 : 0;
+  fs[i] = d ? 0 : 1;
+}
+
+__global__ void k_split_scatter(int64_t E, const int32_t* __restrict__ order,
+                                const int32_t* __restrict__ didx, const int64_t* __restrict__ pd,
+                                const int64_t* __restrict__ ps, int32_t* __restrict__ dorder,
+                                int32_t* __restrict__ sorder) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  const int32_t r = order[i];
+  if (didx[r] >= 0) dorder[pd[i]] = r; else sorder[ps[i]] = r;
+}
+
+}  // namespace
+
+void release_split(mochy_ctx* ctx) {
+  if (!ctx->split_ready && !ctx->dense_idx) return;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->dense_idx) dev_free(ctx, ctx->dense_idx, ctx->split_bytes);
+  if (ctx->nbits) dev_free(ctx, ctx->nbits, ctx->nbits_bytes);
+  if (ctx->dvoff) dev_free(ctx, ctx->dvoff, ctx->dinc_bytes);
+  ctx->dvoff = nullptr;
+  ctx->dvedge = nullptr;
+  ctx->nbits_bytes = ctx->dinc_bytes = 0;
+  ctx->dense_idx = nullptr;
+  ctx->dense_row = nullptr;
+  ctx->dbits = nullptr;
+  ctx->heavy_idx = nullptr;
+  ctx->nbits = nullptr;
+  ctx->sbits = nullptr;
+  ctx->dense_order = ctx->sparse_order = nullptr;
+  ctx->split_bytes = 0;
+  ctx->split_ready = false;
+  ctx->n_dense = ctx->n_sparse = ctx->n_heavy = ctx->wwords = 0;
+}
+
+int choose_dense_threshold(mochy_ctx* ctx);   // tune.cu
+
+size_t dense_smem_bytes(int64_t W) {
+  return 432 * 8 + 2192 * 2 + 64 * 4 + sizeof(WarpScratch) * kWarps + (size_t)W * 8;
+}
+
+size_t sparse_smem_bytes(int max_deg) {
+  return 432 * 8 + 2192 * 2 + 64 * 4 + 64 * 4 * kWarps + (size_t)max_deg * 13 + 16;
+}
+
+int prepare_split(mochy_ctx* ctx) {
+  if (ctx->split_ready) return MOCHY_OK;
+  const int64_t E = ctx->n_edges, N = ctx->n_nodes;
+  cudaStream_t st = ctx->stream;
+  const int thr = ctx->dense_thr > 0 ? ctx->dense_thr : choose_dense_threshold(ctx);
+  if (thr <= 0) return thr < 0 ? thr : fail(MOCHY_E_UNSUPPORTED, "no usable dense threshold");
+  // dense rows
+  void* t;
+  MOCHY_TRY(scratch(ctx, 0, (size_t)(std::max(E, N) + 2) * 8 * 4, &t));
+  int64_t* flag = (int64_t*)t;
+  int64_t* pos = flag + std::max(E, N) + 2;
+  int64_t* flag2 = pos + std::max(E, N) + 2;
+  int64_t* pos2 = flag2 + std::max(E, N) + 2;
+  k_dense_flags<<<ceil_div(E + 1, 256), 256, 0, st>>>(E, ctx->noff, thr, flag);
+  MOCHY_LAUNCHED();
+  MOCHY_TRY(scan_exclusive_i64(ctx, flag, pos, E + 1));
+  int64_t n_dense = 0;
+  MOCHY_CUDA(cudaMemcpyAsync(&n_dense, pos + E, 8, cudaMemcpyDeviceToHost, st));
+  MOCHY_CUDA(cudaStreamSynchronize(st));
+  const int64_t W = std::max<int64_t>((n_dense + 31) / 32, 1);
+  if (dense_smem_bytes(W) + 1024 > ctx->smem_optin)
+    return fail(MOCHY_E_UNSUPPORTED, "too many dense rows for the shared-memory bitmap");
+  // heavy nodes need dense indices first: allocate everything in one block
+  // (sizes of the heavy part are bounded by N)
+  const int64_t nd1 = std::max<int64_t>(n_dense, 1);
+  size_t off_idx = 0;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t b_didx = al((size_t)std::max<int64_t>(E, 1) * 4);
+  const size_t b_drow = al((size_t)nd1 * 4);
+  const size_t b_dbits = al((size_t)nd1 * 2 * W * 4);
+  const size_t b_hidx = al((size_t)std::max<int64_t>(N, 1) * 4);
+  const size_t b_sbits = al((size_t)kClasses * W * 4);
+  const size_t b_ord = al((size_t)std::max<int64_t>(E, 1) * 4);
+  const size_t head = b_didx + b_drow + b_dbits + b_hidx + b_sbits + 2 * b_ord;
+  (void)off_idx;
+  // count heavy nodes before sizing their bitmaps: needs dense_idx, so build
+  // the head block first
+  void* p;
+  MOCHY_TRY(dev_alloc(ctx, &p, head));
+  char* base = (char*)p;
+  ctx->dense_idx = (int32_t*)base;
+  ctx->dense_row = (int32_t*)(base + b_didx);
+  ctx->dbits = (uint32_t*)(base + b_didx + b_drow);
+  ctx->heavy_idx = (int32_t*)(base + b_didx + b_drow + b_dbits);
+  ctx->sbits = (uint32_t*)(base + b_didx + b_drow + b_dbits + b_hidx);
+  ctx->dense_order = (int32_t*)(base + b_didx + b_drow + b_dbits + b_hidx + b_sbits);
+  ctx->sparse_order = (int32_t*)((char*)ctx->dense_order + b_ord);
+  ctx->split_bytes = head;
+  k_dense_index<<<ceil_div(E, 256), 256, 0, st>>>(E, flag, pos, ctx->dense_idx, ctx->dense_row);
+  MOCHY_LAUNCHED();
+  MOCHY_CUDA(cudaMemsetAsync(ctx->dbits, 0, (size_t)nd1 * 2 * W * 4, st));
+  MOCHY_CUDA(cudaMemsetAsync(ctx->sbits, 0, (size_t)kClasses * W * 4, st));
+  if (n_dense > 0) {
+    k_dense_bits<<<(unsigned)std::min<int64_t>(n_dense, 1 << 16), 256, 0, st>>>(
+        n_dense, W, ctx->dense_row, ctx->eoff, ctx->noff, ctx->nadj, ctx->dense_idx, ctx->dbits);
+    MOCHY_LAUNCHED();
+    k_size_bits<<<ceil_div(n_dense, 256), 256, 0, st>>>(n_dense, W, ctx->dense_row, ctx->eoff,
+                                                         ctx->theta, ctx->sbits);
+    MOCHY_LAUNCHED();
+  }
+  // heavy nodes
+  k_heavy_flags<<<ceil_div(N + 1, 8), 256, 0, st>>>(N, ctx->voff, ctx->vedge, ctx->dense_idx,
+                                                    ctx->heavy_thr, flag2);
+  MOCHY_LAUNCHED();
+  MOCHY_TRY(scan_exclusive_i64(ctx, flag2, pos2, N + 1));
+  int64_t n_heavy = 0;
+  MOCHY_CUDA(cudaMemcpyAsync(&n_heavy, pos2 + N, 8, cudaMemcpyDeviceToHost, st));
+  MOCHY_CUDA(cudaStreamSynchronize(st));
+  if (N > 0) {
+    k_heavy_index<<<ceil_div(N, 256), 256, 0, st>>>(N, flag2, pos2, ctx->heavy_idx);
+    MOCHY_LAUNCHED();
+  }
+  void* nb = nullptr;
+  const size_t b_nbits = (size_t)std::max<int64_t>(n_heavy, 1) * W * 4;
+  int rc = dev_alloc(ctx, &nb, b_nbits);
+  if (rc < 0) {
+    release_split(ctx);
+    return rc;
+  }
+  ctx->nbits = (uint32_t*)nb;
+  ctx->nbits_bytes = b_nbits;
+  MOCHY_CUDA(cudaMemsetAsync(nb, 0, b_nbits, st));
+  if (n_heavy > 0) {
+    k_heavy_bits<<<ceil_div(N, 8), 256, 0, st>>>(N, W, ctx->voff, ctx->vedge, ctx->dense_idx,
+                                                 ctx->heavy_idx, ctx->nbits);
+    MOCHY_LAUNCHED();
+  }
+  // dense incidence lists (for the light nodes)
+  k_dense_count<<<ceil_div(N + 1, 8), 256, 0, st>>>(N, ctx->voff, ctx->vedge, ctx->dense_idx, flag2);
+  MOCHY_LAUNCHED();
+  MOCHY_TRY(scan_exclusive_i64(ctx, flag2, pos2, N + 1));
+  int64_t n_dinc = 0;
+  MOCHY_CUDA(cudaMemcpyAsync(&n_dinc, pos2 + N, 8, cudaMemcpyDeviceToHost, st));
+  MOCHY_CUDA(cudaStreamSynchronize(st));
+  {
+    const size_t b_off = al((size_t)(N + 1) * 8);
+    const size_t bytes = b_off + (size_t)std::max<int64_t>(n_dinc, 1) * 4;
+    void* q;
+    MOCHY_TRY(dev_alloc(ctx, &q, bytes));
+    ctx->dinc_bytes = bytes;
+    ctx->dvoff = (int64_t*)q;
+    ctx->dvedge = (int32_t*)((char*)q + b_off);
+    MOCHY_CUDA(cudaMemcpyAsync(ctx->dvoff, pos2, (size_t)(N + 1) * 8, cudaMemcpyDeviceToDevice, st));
+    if (N > 0) {
+      k_dense_fill<<<ceil_div(N, 8), 256, 0, st>>>(N, ctx->voff, ctx->vedge, ctx->dense_idx,
+                                                   ctx->dvoff, ctx->dvedge);
+      MOCHY_LAUNCHED();
+    }
+  }
+  // work orders
+  k_split_flags<<<ceil_div(E + 1, 256), 256, 0, st>>>(E, ctx->row_order, ctx->dense_idx, flag, flag2);
+  MOCHY_LAUNCHED();
+  MOCHY_TRY(scan_exclusive_i64(ctx, flag, pos, E + 1));
+  MOCHY_TRY(scan_exclusive_i64(ctx, flag2, pos2, E + 1));
+  k_split_scatter<<<ceil_div(E, 256), 256, 0, st>>>(E, ctx->row_order, ctx->dense_idx, pos, pos2,
+                                                    ctx->dense_order, ctx->sparse_order);
+  MOCHY_LAUNCHED();
+  MOCHY_CUDA(cudaStreamSynchronize(st));
+  ctx->n_dense = n_dense;
+  ctx->n_sparse = E - n_dense;
+  ctx->n_heavy = n_heavy;
+  ctx->wwords = W;
+  ctx->dense_thr_used = thr;
+  ctx->split_ready = true;
+  return MOCHY_OK;
+}
+
+int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
+  cudaStream_t st = ctx->stream;
+  MOCHY_TRY(prepare_split(ctx));
+  SplitArgs g;
+  g.n_edges = ctx->n_edges;
+  g.eoff = ctx->eoff;
+  g.enode = ctx->enode;
+  g.voff = ctx->voff;
+  g.vedge = ctx->vedge;
+  g.noff = ctx->noff;
+  g.nadj = ctx->nadj;
+  g.lut3 = ctx->tables.lut3;
+  g.hist = d_hist;
+  g.theta = ctx->theta;
+  g.n_dense = ctx->n_dense;
+  g.wwords = ctx->wwords;
+  g.dense_idx = ctx->dense_idx;
+  g.dense_row = ctx->dense_row;
+  g.dbits = ctx->dbits;
+  g.heavy_idx = ctx->heavy_idx;
+  g.nbits = ctx->nbits;
+  g.sbits = ctx->sbits;
+  g.dvoff = ctx->dvoff;
+  g.dvedge = ctx->dvedge;
+  MOCHY_CUDA(cudaMemsetAsync(ctx->counters, 0, 16 * sizeof(int32_t), st));
+  // open pairs
+  {
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(ctx->n_edges, kOpenWarps),
+                                                      (int64_t)ctx->num_sms * 8);
+    g.order = nullptr;
+    g.n_order = 0;
+    g.queue = nullptr;
+    if (grid > 0) {
+      k_open_pairs<<<grid, kOpenThreads, 0, st>>>(g);
+      MOCHY_LAUNCHED();
+    }
+  }
+  // triangles from sparse rows
+  if (ctx->n_sparse > 0) {
+    const int max_deg = (int)std::min<int64_t>(ctx->max_deg, ctx->dense_thr_used - 1);
+    const size_t smem = sparse_smem_bytes(std::max(max_deg, 1));
+    if (smem + 1024 > ctx->smem_optin)
+      return fail(MOCHY_E_UNSUPPORTED, "sparse rows too long for shared memory");
+    MOCHY_CUDA(cudaFuncSetAttribute(k_sparse_triangles,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_triangles,
+                                                             kThreads, smem));
+    g.order = ctx->sparse_order;
+    g.n_order = ctx->n_sparse;
+    g.queue = ctx->counters + 5;
+    const unsigned grid = (unsigned)std::min<int64_t>((int64_t)ctx->num_sms * std::max(per_sm, 1),
+                                                      ctx->n_sparse);
+    k_sparse_triangles<<<grid, kThreads, smem, st>>>(g, std::max(max_deg, 1));
+    MOCHY_LAUNCHED();
+  }
+  // triangles of dense rows
+  if (ctx->n_dense > 0) {
+    const size_t smem = dense_smem_bytes(ctx->wwords);
+    MOCHY_CUDA(cudaFuncSetAttribute(k_dense_triangles,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_triangles, kThreads,
+                                                             smem));
+    g.order = ctx->dense_order;
+    g.n_order = ctx->n_dense;
+    g.queue = ctx->counters + 6;
+    const unsigned grid = (unsigned)std::min<int64_t>((int64_t)ctx->num_sms * std::max(per_sm, 1),
+                                                      ctx->n_dense);
+    k_dense_triangles<<<grid, kThreads, smem, st>>>(g);
+    MOCHY_LAUNCHED();
+  }
+  return MOCHY_OK;
+}
+
+}  // namespace mochy

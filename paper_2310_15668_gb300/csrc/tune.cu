@@ -1,0 +1,67 @@
+// Choice of the dense-row threshold of the split exact count.
+//
+// A row whose line degree is at least the threshold is "dense": its
+// neighbourhood becomes a bitmap over the dense rows and triangles among
+// dense rows are scanned 32 candidates per word; every other row is staged
+// as a list and its triangles are found by probing.  The tuner evaluates a
+// cost model on the line-degree distribution for every power-of-two
+// threshold the shared-memory limits allow and keeps the cheapest:
+//   dense part  ~ (wedge scans between dense rows) x (words per scan)
+//               ~ 1/2 S_d f_d x W / 3, with S_d the degree mass of dense
+//                 rows, f_d = S_d / S the chance that a neighbour is dense
+//                 and W = n_dense / 32 words;
+//   sparse part ~ sum over sparse rows of deg^2 (pairs of neighbours probed).
+// The relative weight of a word to a probe was measured on GB300 (about 2).
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mochy {
+
+size_t dense_smem_bytes(int64_t W);       // count_split.cu
+size_t sparse_smem_bytes(int max_deg);    // count_split.cu
+
+int choose_dense_threshold(mochy_ctx* ctx) {
+  const int64_t E = ctx->n_edges;
+  std::vector<int64_t> off((size_t)E + 1);
+  MOCHY_CUDA(cudaMemcpyAsync(off.data(), ctx->noff, off.size() * 8, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+  MOCHY_CUDA(cudaStreamSynchronize(ctx->stream));
+  std::vector<int64_t> deg((size_t)E);
+  double S = 0.0;
+  for (int64_t i = 0; i < E; ++i) {
+    deg[i] = off[i + 1] - off[i];
+    S += (double)deg[i];
+  }
+  const double word_weight = 2.0;
+  int best = -1;
+  double best_cost = 0.0;
+  for (int64_t thr = 32; thr <= (int64_t)1 << 20; thr <<= 1) {
+    int64_t nd = 0, max_sparse = 0;
+    double Sd = 0.0, sparse = 0.0;
+    for (int64_t i = 0; i < E; ++i) {
+      if (deg[i] >= thr) {
+        ++nd;
+        Sd += (double)deg[i];
+      } else {
+        sparse += (double)deg[i] * (double)deg[i];
+        max_sparse = std::max(max_sparse, deg[i]);
+      }
+    }
+    const int64_t W = std::max<int64_t>((nd + 31) / 32, 1);
+    if (dense_smem_bytes(W) + 1024 > ctx->smem_optin) continue;
+    if (sparse_smem_bytes((int)std::max<int64_t>(max_sparse, 1)) + 1024 > ctx->smem_optin) continue;
+    const double fd = S > 0 ? Sd / S : 0.0;
+    const double cost = word_weight * 0.5 * Sd * fd * (double)W / 3.0 + sparse;
+    if (best < 0 || cost < best_cost) {
+      best = (int)thr;
+      best_cost = cost;
+    }
+    if (nd == 0) break;   // larger thresholds change nothing
+  }
+  if (best < 0) return fail(MOCHY_E_UNSUPPORTED, "no dense threshold fits shared memory");
+  return best;
+}
+
+}  // namespace mochy

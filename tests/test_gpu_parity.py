@@ -74,25 +74,63 @@ def test_load_and_project(ctx, name):
     assert np.array_equal(ctx.line_degrees(), odeg)
 
 
+# exact-count kernels: the per-hyperwedge scan, and the split kernel with the
+# tuned threshold, with (nearly) every row dense, and with a middle threshold
+VARIANTS = {"scan": dict(exact_kernel=1), "split": dict(), "dense": dict(dense_threshold=2),
+            "mixed": dict(dense_threshold=24)}
+
+
+@pytest.fixture(scope="module")
+def variant_ctx():
+    ctxs = {k: B.Context(**v) for k, v in VARIANTS.items()}
+    yield ctxs
+    for c in ctxs.values():
+        c.close()
+
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
 @pytest.mark.parametrize("name", sorted(GRAPHS))
-def test_exact_counts(ctx, name):
+def test_exact_counts(variant_ctx, name, variant):
+    c = variant_ctx[variant]
     n, off, nodes = GRAPHS[name]
-    ctx.load(n, off, nodes)
-    ctx.project()
-    h, h3 = ctx.count_exact()
+    c.load(n, off, nodes)
+    c.project()
+    h, h3 = c.count_exact()
     oh, o3 = _oracle_exact(name)
     assert np.array_equal(h3, o3)
     assert np.array_equal(h, oh)
 
 
+def test_split_matches_scan_on_larger_zipf_graph(variant_ctx):
+    """GPU against GPU where the oracle is too slow: 20,000 hyperedges with a
+    hub of about 4,500 hyperedges; every kernel variant gives the same counts,
+    and the open/closed totals satisfy the line-graph degree identity."""
+    spec = synth.HypergraphSpec(10_000, 20_000, 2, 25, "powerlaw", 2.5, "zipf", 1.0, seed=5)
+    off, nodes = synth.generate(spec)
+    res = {}
+    for v, c in variant_ctx.items():
+        c.load(spec.n_nodes, off, nodes)
+        c.project()
+        res[v] = c.count_exact()
+    for v in res:
+        assert np.array_equal(res[v][1], res["scan"][1]), v
+    T = oracle.tables()
+    h = res["split"][0]
+    deg = variant_ctx["split"].line_degrees()
+    op = int(sum(h[t] for t in range(26) if T["h_open"][t]))
+    assert op + 3 * (int(h.sum()) - op) == int((deg * (deg - 1) // 2).sum())
+
+
 @pytest.mark.parametrize("theta", [2, 3])
-def test_exact_counts_other_theta(theta):
-    n, off, nodes = GRAPHS["wide"]
-    with B.Context(theta=theta) as c:
+@pytest.mark.parametrize("variant", ["scan", "split", "dense"])
+@pytest.mark.parametrize("name", ["wide", "zipf_small"])
+def test_exact_counts_other_theta(theta, variant, name):
+    n, off, nodes = GRAPHS[name]
+    with B.Context(theta=theta, **VARIANTS[variant]) as c:
         c.load(n, off, nodes)
         c.project()
         h, h3 = c.count_exact()
-    oh, o3 = oracle.count_exact(off, nodes, theta=theta)
+    oh, o3 = _oracle_exact(name, theta)
     assert np.array_equal(h3, o3) and np.array_equal(h, oh)
 
 
