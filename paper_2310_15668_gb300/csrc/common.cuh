@@ -117,6 +117,7 @@ struct mochy_ctx {
   int32_t* sparse_order = nullptr;  // sparse rows by decreasing work
   int64_t* dvoff = nullptr;         // [N+1] dense members of E_v ...
   int32_t* dvedge = nullptr;        // ... as dense indices, ascending
+  uint8_t* dsize = nullptr;         // [n_dense] |e_k| of dense rows
   size_t split_bytes = 0, nbits_bytes = 0, dinc_bytes = 0;
   int32_t dense_thr_used = 0;
 

@@ -99,6 +99,7 @@ struct SplitArgs {
   const uint32_t* sbits;
   const int64_t* dvoff;
   const int32_t* dvedge;
+  const uint8_t* dsize;
   const int32_t* order;
   int64_t n_order;
   int32_t* queue;
@@ -207,30 +208,80 @@ __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
 }
 
 // ---------------------------------------------------------------------------
-// Triangles with three dense rows: CTA per dense row a.
-// Shared layout: hist | lut | anodes[64] | per-warp (bnodes[64], ihv[64],
-// ilv[64], meta[4]) | A1[W] | A2[W]
+// Triangles with three dense rows: CTA per dense row a, warp per hyperwedge
+// (a, b).  Every node of e_a | e_b falls in one of three groups: in e_a only
+// (A), in e_b only (B) or in both (T).  For a candidate e_k adjacent to both,
+//   omega_ak = xa + xt,  omega_bk = xb + xt,  |e_a & e_b & e_k| = xt,
+// where xa, xb, xt count the nodes of each group that e_k holds.  For the
+// nodes with a bitmap ("heavy") these counts are kept bit-sliced, 32
+// candidates per word (2 bits each plus an overflow flag).  The two usual
+// cases, (xa, xb, xt) = (0, 0, 1) and (1, 1, 0), are counted by popcount per
+// size class; any other case goes to a per-warp table keyed by (xa, xb, xt,
+// effective size); a candidate whose counts overflow is classified from its
+// node list.  Candidates that hold a node without bitmap ("light") are
+// corrected afterwards from the short dense incidence lists of those nodes:
+// the class the word loop gave them is taken out and the exact one put in.
+// Shared layout: hist | lut | anodes[64] | WarpScratch[kDWarps] | A1[W]
 // ---------------------------------------------------------------------------
+constexpr int kDThreads = 256;
+constexpr int kDWarps = kDThreads / 32;
+constexpr int kCeff = 16;          // effective sizes kept in the table
+constexpr int kCombo = 64;         // (xa, xb, xt), 2 bits each
+
 struct WarpScratch {
   int32_t bnodes[64];
-  int32_t ihv[64];
-  int32_t ilv[64];
-  int32_t meta[4];
+  int32_t hidx[3][64];   // heavy indices of groups A, B, T
+  int32_t light[128];    // light nodes of e_a | e_b
+  int32_t lgrp[128];     // their group (0 A, 1 B, 2 T)
+  int32_t n[5];          // nA, nB, nT, nlight, pad
+  uint32_t table[kCombo * kCeff];
 };
 
-__global__ void __launch_bounds__(kThreads) k_dense_triangles(SplitArgs g) {
+__device__ __forceinline__ void slice_add(uint32_t& c0, uint32_t& c1, uint32_t& ovf, uint32_t m) {
+  const uint32_t k0 = c0 & m;
+  c0 ^= m;
+  ovf |= c1 & k0;
+  c1 ^= k0;
+}
+
+__device__ __forceinline__ int sval(uint32_t c0, uint32_t c1, int bit) {
+  return (int)((c0 >> bit) & 1u) + 2 * (int)((c1 >> bit) & 1u);
+}
+
+// exact overlaps of e_k with e_a and e_b (and the part through heavy nodes)
+struct Overlap {
+  int z, y, t, hz, hy, ht;
+};
+
+__device__ __forceinline__ Overlap overlaps(const int32_t* anodes, int A, const int32_t* bnodes,
+                                            int B, const int32_t* knodes, int C,
+                                            const int32_t* heavy_idx) {
+  Overlap o{0, 0, 0, 0, 0, 0};
+  for (int q = 0; q < C; ++q) {
+    const int32_t u = knodes[q];
+    const bool ia = has_node(anodes, A, u), ib = has_node(bnodes, B, u);
+    if (!ia && !ib) continue;
+    const bool hv = heavy_idx[u] >= 0;
+    o.z += ia; o.y += ib; o.t += ia && ib;
+    if (hv) { o.hz += ia; o.hy += ib; o.ht += ia && ib; }
+  }
+  return o;
+}
+
+__global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* hist = (unsigned long long*)smem;
   uint16_t* lut = (uint16_t*)(hist + 432);
   int32_t* anodes = (int32_t*)(lut + 2192);
   WarpScratch* ws = (WarpScratch*)(anodes + 64);
-  uint32_t* A1 = (uint32_t*)(ws + kWarps);
+  uint32_t* A1 = (uint32_t*)(ws + kDWarps);
   const int64_t W = g.wwords;
-  uint32_t* A2 = A1 + W;
   __shared__ int64_t slot_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpScratch& me = ws[warp];
   load_lut(lut, g.lut3, hist);
+  for (int q = lane; q < kCombo * kCeff; q += 32) me.table[q] = 0u;
+  const int theta = g.theta;
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) slot_s = atomicAdd(g.queue, 1);
@@ -242,17 +293,14 @@ __global__ void __launch_bounds__(kThreads) k_dense_triangles(SplitArgs g) {
     const int64_t rb = g.noff[a], re = g.noff[a + 1];
     const int A = (int)(g.eoff[a + 1] - g.eoff[a]);
     if (threadIdx.x < A) anodes[threadIdx.x] = g.enode[g.eoff[a] + threadIdx.x];
-    for (int64_t q = threadIdx.x; q < 2 * W; q += kThreads) A1[q] = 0u;
+    for (int64_t q = threadIdx.x; q < W; q += kDThreads) A1[q] = 0u;
     __syncthreads();
-    for (int64_t p = rb + threadIdx.x; p < re; p += kThreads) {
-      const uint2 e = g.nadj[p];
-      const int kd = g.dense_idx[ent_id(e)];
-      if (kd < 0) continue;
-      atomicOr(&A1[kd >> 5], 1u << (kd & 31));
-      if (entry_omega(e.y, A) >= 2) atomicOr(&A2[kd >> 5], 1u << (kd & 31));
+    for (int64_t p = rb + threadIdx.x; p < re; p += kDThreads) {
+      const int kd = g.dense_idx[ent_id(g.nadj[p])];
+      if (kd >= 0) atomicOr(&A1[kd >> 5], 1u << (kd & 31));
     }
     __syncthreads();
-    for (int64_t idx = rb + warp; idx < re; idx += kWarps) {
+    for (int64_t idx = rb + warp; idx < re; idx += kDWarps) {
       const uint2 eab = g.nadj[idx];
       const int64_t b = ent_id(eab);
       const int bd = g.dense_idx[b];
@@ -260,25 +308,43 @@ __global__ void __launch_bounds__(kThreads) k_dense_triangles(SplitArgs g) {
       const int B = ent_size(eab);
       const int x = entry_omega(eab.y, A);
       if (lane < B) me.bnodes[lane] = g.enode[g.eoff[b] + lane];
-      if (B > 32 && lane + 32 < B) me.bnodes[lane + 32] = g.enode[g.eoff[b] + lane + 32];
+      if (lane + 32 < B) me.bnodes[lane + 32] = g.enode[g.eoff[b] + lane + 32];
+      if (lane < 5) me.n[lane] = 0;
       __syncwarp();
-      // e_a & e_b split into heavy nodes (bitmaps) and light nodes (lists)
-      int nh = 0, nl = 0;
-      for (int base = 0; base < B; base += 32) {
+      // groups of the nodes of e_a | e_b
+      for (int base = 0; base < A + B; base += 32) {
         const int l = base + lane;
-        const int32_t u = l < B ? me.bnodes[l] : -1;
-        const bool common = l < B && has_node(anodes, A, u);
-        const int hv = common ? g.heavy_idx[u] : -1;
-        const unsigned bh = __ballot_sync(0xffffffffu, common && hv >= 0);
-        const unsigned bl = __ballot_sync(0xffffffffu, common && hv < 0);
-        if (common && hv >= 0) me.ihv[nh + __popc(bh & ((1u << lane) - 1u))] = hv;
-        if (common && hv < 0) me.ilv[nl + __popc(bl & ((1u << lane) - 1u))] = u;
-        nh += __popc(bh);
-        nl += __popc(bl);
+        int32_t u = -1;
+        int grp = -1;
+        if (l < A) {
+          u = anodes[l];
+          grp = has_node(me.bnodes, B, u) ? 2 : 0;
+        } else if (l < A + B) {
+          u = me.bnodes[l - A];
+          grp = has_node(anodes, A, u) ? -1 : 1;     // common nodes come from e_a
+        }
+        const int hv = grp >= 0 ? g.heavy_idx[u] : -1;
+        for (int gg = 0; gg < 3; ++gg) {
+          const bool mine = grp == gg && hv >= 0;
+          const unsigned bal = __ballot_sync(0xffffffffu, mine);
+          if (mine) me.hidx[gg][me.n[gg] + __popc(bal & ((1u << lane) - 1u))] = hv;
+          __syncwarp();
+          if (lane == 0) me.n[gg] += __popc(bal);
+          __syncwarp();
+        }
+        const bool lt = grp >= 0 && hv < 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, lt);
+        if (lt) {
+          const int pos = me.n[3] + __popc(bal & ((1u << lane) - 1u));
+          me.light[pos] = u;
+          me.lgrp[pos] = grp;
+        }
+        __syncwarp();
+        if (lane == 0) me.n[3] += __popc(bal);
+        __syncwarp();
       }
-      __syncwarp();
+      const int nA = me.n[0], nB = me.n[1], nT = me.n[2], nL = me.n[3];
       const uint32_t* B1 = g.dbits + (int64_t)bd * 2 * W;
-      const uint32_t* B2 = B1 + W;
       long long c0[kClasses], c1[kClasses];
 #pragma unroll
       for (int c = 0; c < kClasses; ++c) { c0[c] = 0; c1[c] = 0; }
@@ -288,12 +354,16 @@ __global__ void __launch_bounds__(kThreads) k_dense_triangles(SplitArgs g) {
         uint32_t m = A1[w] & __ldg(&B1[w]);
         if (w == fw) m &= 0xffffffffu << (first & 31);
         if (!m) continue;
-        const uint32_t ex = m & (A2[w] | __ldg(&B2[w]));
-        const uint32_t simple = m & ~ex;
-        if (simple) {
-          uint32_t T = 0u;
-          for (int h = 0; h < nh; ++h) T |= __ldg(&g.nbits[(int64_t)me.ihv[h] * W + w]);
-          const uint32_t s1 = simple & T, s0 = simple & ~T;
+        uint32_t a0 = 0, a1 = 0, b0 = 0, b1 = 0, t0 = 0, t1 = 0, ovf = 0;
+        for (int h = 0; h < nA; ++h) slice_add(a0, a1, ovf, __ldg(&g.nbits[(int64_t)me.hidx[0][h] * W + w]));
+        for (int h = 0; h < nB; ++h) slice_add(b0, b1, ovf, __ldg(&g.nbits[(int64_t)me.hidx[1][h] * W + w]));
+        for (int h = 0; h < nT; ++h) slice_add(t0, t1, ovf, __ldg(&g.nbits[(int64_t)me.hidx[2][h] * W + w]));
+        const uint32_t za = a0 | a1, zb = b0 | b1, zt = t0 | t1;
+        ovf &= m;
+        const uint32_t valid = m & (za | zt) & (zb | zt) & ~ovf;
+        const uint32_t s1 = valid & ~za & ~zb & t0 & ~t1;                 // (0, 0, 1)
+        const uint32_t s0 = valid & a0 & ~a1 & b0 & ~b1 & ~zt;            // (1, 1, 0)
+        if (s1 | s0) {
 #pragma unroll
           for (int c = 0; c < kClasses; ++c) {
             const uint32_t sc = __ldg(&g.sbits[(int64_t)c * W + w]);
@@ -301,40 +371,56 @@ __global__ void __launch_bounds__(kThreads) k_dense_triangles(SplitArgs g) {
             c0[c] += __popc(s0 & sc);
           }
         }
-        uint32_t e = ex;
+        uint32_t rest = valid & ~s1 & ~s0;
+        while (rest) {
+          const int bit = __ffs(rest) - 1;
+          rest &= rest - 1;
+          const int xa = sval(a0, a1, bit), xb = sval(b0, b1, bit), xt = sval(t0, t1, bit);
+          const int C = g.dsize[w * 32 + bit];
+          // every size-dependent region subtracts at most xa + xb + 2 xt from
+          // |e_k|, so sizes beyond that plus theta + 1 all give the same codes
+          const int ce = min(C, xa + xb + 2 * xt + theta + 1);
+          if (ce <= kCeff) {
+            atomicAdd(&me.table[((xa * 4 + xb) * 4 + xt) * kCeff + ce - 1], 1u);
+          } else {
+            add_triangle(hist, lut, theta, A, B, C, x, xb + xt, xa + xt, xt, 1);
+          }
+        }
+        uint32_t e = ovf;
         while (e) {
           const int bit = __ffs(e) - 1;
           e &= e - 1;
           const int64_t k = g.dense_row[w * 32 + bit];
           const int64_t kb = g.eoff[k];
           const int C = (int)(g.eoff[k + 1] - kb);
-          int y = 0, z = 0, t = 0;
-          for (int q = 0; q < C; ++q) {
-            const int32_t u = g.enode[kb + q];
-            const bool ia = has_node(anodes, A, u), ib = has_node(me.bnodes, B, u);
-            z += ia; y += ib; t += ia && ib;
-          }
-          add_triangle(hist, lut, g.theta, A, B, C, x, y, z, t, 1);
+          const Overlap o = overlaps(anodes, A, me.bnodes, B, g.enode + kb, C, g.heavy_idx);
+          if (o.z != o.hz || o.y != o.hy) continue;   // light-touched: handled below
+          add_triangle(hist, lut, theta, A, B, C, x, o.y, o.z, o.t, 1);
         }
       }
-      // candidates through a light node of e_a & e_b: simple ones have t = 1
-      for (int l = 0; l < nl; ++l) {
-        const int32_t v = me.ilv[l];
+      // candidates holding a light node: replace the word loop's class by the
+      // exact one (each candidate once: it is handled at its first light node)
+      for (int l = 0; l < nL; ++l) {
+        const int32_t v = me.light[l];
         for (int64_t q = g.dvoff[v] + lane; q < g.dvoff[v + 1]; q += 32) {
           const int kd = g.dvedge[q];
           if (kd <= bd) continue;
-          const int64_t k = g.dense_row[kd];
           const int w = kd >> 5;
           const uint32_t bit = 1u << (kd & 31);
           if (!(A1[w] & __ldg(&B1[w]) & bit)) continue;
-          if ((A2[w] | __ldg(&B2[w])) & bit) continue;
-          uint32_t T = 0u;
-          for (int h = 0; h < nh; ++h) T |= __ldg(&g.nbits[(int64_t)me.ihv[h] * W + w]);
-          if (T & bit) continue;
-          const int c = size_class((int)(g.eoff[k + 1] - g.eoff[k]), g.theta);
-#pragma unroll
-          for (int cc = 0; cc < kClasses; ++cc)
-            if (cc == c) { c0[cc] -= 1; c1[cc] += 1; }
+          const int64_t k = g.dense_row[kd];
+          const int64_t kb = g.eoff[k];
+          const int C = (int)(g.eoff[k + 1] - kb);
+          bool seen = false;
+          for (int l2 = 0; l2 < l && !seen; ++l2) seen = has_node(g.enode + kb, C, me.light[l2]);
+          if (seen) continue;
+          const Overlap o = overlaps(anodes, A, me.bnodes, B, g.enode + kb, C, g.heavy_idx);
+          const bool hovf = o.hz - o.ht > 3 || o.hy - o.ht > 3 || o.ht > 3;
+          if (!hovf && o.hz >= 1 && o.hy >= 1) {
+            // counted by the word loop with the heavy-node overlaps
+            add_triangle(hist, lut, theta, A, B, C, x, o.hy, o.hz, o.ht, -1);
+          }
+          add_triangle(hist, lut, theta, A, B, C, x, o.y, o.z, o.t, 1);
         }
       }
 #pragma unroll
@@ -345,10 +431,19 @@ __global__ void __launch_bounds__(kThreads) k_dense_triangles(SplitArgs g) {
           v1 += __shfl_xor_sync(0xffffffffu, v1, d);
         }
         if (lane == 0) {
-          const int C = class_rep(c, g.theta);
-          if (v0) add_triangle(hist, lut, g.theta, A, B, C, x, 1, 1, 0, v0);
-          if (v1) add_triangle(hist, lut, g.theta, A, B, C, x, 1, 1, 1, v1);
+          const int C = class_rep(c, theta);
+          if (v0) add_triangle(hist, lut, theta, A, B, C, x, 1, 1, 0, v0);
+          if (v1) add_triangle(hist, lut, theta, A, B, C, x, 1, 1, 1, v1);
         }
+      }
+      __syncwarp();
+      for (int q = lane; q < kCombo * kCeff; q += 32) {
+        const uint32_t n = me.table[q];
+        if (!n) continue;
+        me.table[q] = 0u;
+        const int ce = q % kCeff + 1, combo = q / kCeff;
+        const int xt = combo & 3, xb = (combo >> 2) & 3, xa = combo >> 4;
+        add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, (long long)n);
       }
       __syncwarp();
     }
@@ -573,10 +668,12 @@ __global__ void k_dense_fill(int64_t N, const int64_t* __restrict__ voff,
 }
 
 __global__ void k_size_bits(int64_t n_dense, int64_t W, const int32_t* __restrict__ drow,
-                            const int64_t* __restrict__ eoff, int theta, uint32_t* __restrict__ sbits) {
+                            const int64_t* __restrict__ eoff, int theta, uint32_t* __restrict__ sbits,
+                            uint8_t* __restrict__ dsize) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_dense) return;
   const int64_t k = drow[r];
+  dsize[r] = (uint8_t)(eoff[k + 1] - eoff[k]);
   const int c = size_class((int)(eoff[k + 1] - eoff[k]), theta);
   atomicOr(&sbits[(int64_t)c * W + (r >> 5)], 1u << (r & 31));
 }
@@ -621,6 +718,7 @@ void release_split(mochy_ctx* ctx) {
   ctx->nbits = nullptr;
   ctx->sbits = nullptr;
   ctx->dense_order = ctx->sparse_order = nullptr;
+  ctx->dsize = nullptr;
   ctx->split_bytes = 0;
   ctx->split_ready = false;
   ctx->n_dense = ctx->n_sparse = ctx->n_heavy = ctx->wwords = 0;
@@ -629,7 +727,7 @@ void release_split(mochy_ctx* ctx) {
 int choose_dense_threshold(mochy_ctx* ctx);   // tune.cu
 
 size_t dense_smem_bytes(int64_t W) {
-  return 432 * 8 + 2192 * 2 + 64 * 4 + sizeof(WarpScratch) * kWarps + (size_t)W * 8;
+  return 432 * 8 + 2192 * 2 + 64 * 4 + sizeof(WarpScratch) * kDWarps + (size_t)W * 4;
 }
 
 size_t sparse_smem_bytes(int max_deg) {
@@ -669,7 +767,8 @@ int prepare_split(mochy_ctx* ctx) {
   const size_t b_hidx = al((size_t)std::max<int64_t>(N, 1) * 4);
   const size_t b_sbits = al((size_t)kClasses * W * 4);
   const size_t b_ord = al((size_t)std::max<int64_t>(E, 1) * 4);
-  const size_t head = b_didx + b_drow + b_dbits + b_hidx + b_sbits + 2 * b_ord;
+  const size_t b_dsize = al((size_t)nd1);
+  const size_t head = b_didx + b_drow + b_dbits + b_hidx + b_sbits + 2 * b_ord + b_dsize;
   (void)off_idx;
   // count heavy nodes before sizing their bitmaps: needs dense_idx, so build
   // the head block first
@@ -683,6 +782,7 @@ int prepare_split(mochy_ctx* ctx) {
   ctx->sbits = (uint32_t*)(base + b_didx + b_drow + b_dbits + b_hidx);
   ctx->dense_order = (int32_t*)(base + b_didx + b_drow + b_dbits + b_hidx + b_sbits);
   ctx->sparse_order = (int32_t*)((char*)ctx->dense_order + b_ord);
+  ctx->dsize = (uint8_t*)((char*)ctx->sparse_order + b_ord);
   ctx->split_bytes = head;
   k_dense_index<<<ceil_div(E, 256), 256, 0, st>>>(E, flag, pos, ctx->dense_idx, ctx->dense_row);
   MOCHY_LAUNCHED();
@@ -693,7 +793,7 @@ int prepare_split(mochy_ctx* ctx) {
         n_dense, W, ctx->dense_row, ctx->eoff, ctx->noff, ctx->nadj, ctx->dense_idx, ctx->dbits);
     MOCHY_LAUNCHED();
     k_size_bits<<<ceil_div(n_dense, 256), 256, 0, st>>>(n_dense, W, ctx->dense_row, ctx->eoff,
-                                                         ctx->theta, ctx->sbits);
+                                                         ctx->theta, ctx->sbits, ctx->dsize);
     MOCHY_LAUNCHED();
   }
   // heavy nodes
@@ -787,6 +887,7 @@ int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
   g.sbits = ctx->sbits;
   g.dvoff = ctx->dvoff;
   g.dvedge = ctx->dvedge;
+  g.dsize = ctx->dsize;
   MOCHY_CUDA(cudaMemsetAsync(ctx->counters, 0, 16 * sizeof(int32_t), st));
   // open pairs
   {
@@ -825,14 +926,14 @@ int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
     MOCHY_CUDA(cudaFuncSetAttribute(k_dense_triangles,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_triangles, kThreads,
+    MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_triangles, kDThreads,
                                                              smem));
     g.order = ctx->dense_order;
     g.n_order = ctx->n_dense;
     g.queue = ctx->counters + 6;
     const unsigned grid = (unsigned)std::min<int64_t>((int64_t)ctx->num_sms * std::max(per_sm, 1),
                                                       ctx->n_dense);
-    k_dense_triangles<<<grid, kThreads, smem, st>>>(g);
+    k_dense_triangles<<<grid, kDThreads, smem, st>>>(g);
     MOCHY_LAUNCHED();
   }
   return MOCHY_OK;
