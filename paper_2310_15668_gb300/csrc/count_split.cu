@@ -17,14 +17,17 @@
 //
 // Closed instances (triangles of the line graph) are enumerated once each,
 // from their smallest member in the order "sparse rows (by id) before dense
-// rows (by id)", where a row is dense when its line degree is at least a
-// threshold.  A triangle of three dense rows is found with bitmaps over the
+// rows (by line degree, then id)", where a row is dense when its line degree
+// is at least a threshold.  A triangle of three dense rows is found with bitmaps over the
 // dense rows: 32 candidate third hyperedges per word, and when both overlaps
 // with the candidate are 1 the triple intersection is whether the candidate
 // holds a node of e_a & e_b (node bitmaps), so such candidates are counted by
 // popcount per (triple intersection, size class).  Every other candidate is
 // classified exactly from node lists.  Triangles with a sparse smallest member
 // are enumerated from a staged copy of that member's row.
+#include <cstdio>
+#include <cstdlib>
+
 #include "classify.cuh"
 
 namespace mochy {
@@ -100,6 +103,7 @@ struct SplitArgs {
   const int64_t* dvoff;
   const int32_t* dvedge;
   const uint8_t* dsize;
+  const uint32_t* cbits;     // [5][W] size classes (theta other than 1)
   const int32_t* order;
   int64_t n_order;
   int32_t* queue;
@@ -268,6 +272,25 @@ __device__ __forceinline__ Overlap overlaps(const int32_t* anodes, int A, const 
   return o;
 }
 
+// Counting of the usual overlap combinations by popcount.  With theta = 1
+// the combinations (xa, xb, xt) = (0,0,1), (0,1,1), (1,0,1), (1,1,0) are
+// counted per effective size (|e_k| capped where all codes stop changing:
+// 4, 5, 5 and 4); with another theta only (0,0,1) and (1,1,0) are, per size
+// class.  Bit-planes p0..p3 hold min(|e_k|, 15) of the candidates.
+struct SizeMasks {
+  uint32_t e1, e2, e3, e4, ge4, ge5;
+  __device__ __forceinline__ SizeMasks(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3) {
+    const uint32_t lo = ~p3 & ~p2;
+    e1 = lo & ~p1 & p0;
+    e2 = lo & p1 & ~p0;
+    e3 = lo & p1 & p0;
+    e4 = ~p3 & p2 & ~p1 & ~p0;
+    ge4 = p3 | p2;
+    ge5 = ge4 & ~e4;
+  }
+};
+
+template <bool kTheta1>
 __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* hist = (unsigned long long*)smem;
@@ -282,6 +305,10 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
   load_lut(lut, g.lut3, hist);
   for (int q = lane; q < kCombo * kCeff; q += 32) me.table[q] = 0u;
   const int theta = g.theta;
+  const uint32_t* P0 = g.sbits;
+  const uint32_t* P1 = g.sbits + W;
+  const uint32_t* P2 = g.sbits + 2 * W;
+  const uint32_t* P3 = g.sbits + 3 * W;
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) slot_s = atomicAdd(g.queue, 1);
@@ -337,7 +364,6 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         if (lt) {
           const int pos = me.n[3] + __popc(bal & ((1u << lane) - 1u));
           me.light[pos] = u;
-          me.lgrp[pos] = grp;
         }
         __syncwarp();
         if (lane == 0) me.n[3] += __popc(bal);
@@ -345,9 +371,11 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       }
       const int nA = me.n[0], nB = me.n[1], nT = me.n[2], nL = me.n[3];
       const uint32_t* B1 = g.dbits + (int64_t)bd * 2 * W;
-      long long c0[kClasses], c1[kClasses];
+      // per-lane counters: q001[4], q011[5], q101[5], q110[4] (theta = 1) or
+      // q001[5], q110[5] by size class (other theta)
+      uint32_t cnt[18];
 #pragma unroll
-      for (int c = 0; c < kClasses; ++c) { c0[c] = 0; c1[c] = 0; }
+      for (int c = 0; c < 18; ++c) cnt[c] = 0u;
       const int64_t first = (int64_t)(bd + 1);
       const int64_t fw = first >> 5;
       for (int64_t w = fw + lane; w < W; w += 32) {
@@ -361,24 +389,42 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         const uint32_t za = a0 | a1, zb = b0 | b1, zt = t0 | t1;
         ovf &= m;
         const uint32_t valid = m & (za | zt) & (zb | zt) & ~ovf;
-        const uint32_t s1 = valid & ~za & ~zb & t0 & ~t1;                 // (0, 0, 1)
-        const uint32_t s0 = valid & a0 & ~a1 & b0 & ~b1 & ~zt;            // (1, 1, 0)
-        if (s1 | s0) {
+        const uint32_t one_a = a0 & ~a1, one_b = b0 & ~b1, one_t = t0 & ~t1;
+        const uint32_t s001 = valid & ~za & ~zb & one_t;
+        const uint32_t s110 = valid & one_a & one_b & ~zt;
+        uint32_t done = s001 | s110;
+        const uint32_t p0 = __ldg(&P0[w]), p1 = __ldg(&P1[w]), p2 = __ldg(&P2[w]), p3 = __ldg(&P3[w]);
+        const SizeMasks sz(p0, p1, p2, p3);
+        if (kTheta1) {
+          const uint32_t s011 = valid & ~za & one_b & one_t;
+          const uint32_t s101 = valid & one_a & ~zb & one_t;
+          done |= s011 | s101;
+          cnt[0] += __popc(s001 & sz.e1); cnt[1] += __popc(s001 & sz.e2);
+          cnt[2] += __popc(s001 & sz.e3); cnt[3] += __popc(s001 & sz.ge4);
+          cnt[4] += __popc(s011 & sz.e1); cnt[5] += __popc(s011 & sz.e2);
+          cnt[6] += __popc(s011 & sz.e3); cnt[7] += __popc(s011 & sz.e4);
+          cnt[8] += __popc(s011 & sz.ge5);
+          cnt[9] += __popc(s101 & sz.e1); cnt[10] += __popc(s101 & sz.e2);
+          cnt[11] += __popc(s101 & sz.e3); cnt[12] += __popc(s101 & sz.e4);
+          cnt[13] += __popc(s101 & sz.ge5);
+          cnt[14] += __popc(s110 & sz.e1); cnt[15] += __popc(s110 & sz.e2);
+          cnt[16] += __popc(s110 & sz.e3); cnt[17] += __popc(s110 & sz.ge4);
+        } else {
 #pragma unroll
           for (int c = 0; c < kClasses; ++c) {
-            const uint32_t sc = __ldg(&g.sbits[(int64_t)c * W + w]);
-            c1[c] += __popc(s1 & sc);
-            c0[c] += __popc(s0 & sc);
+            const uint32_t sc = __ldg(&g.cbits[(int64_t)c * W + w]);
+            cnt[c] += __popc(s001 & sc);
+            cnt[5 + c] += __popc(s110 & sc);
           }
         }
-        uint32_t rest = valid & ~s1 & ~s0;
+        uint32_t rest = valid & ~done;
         while (rest) {
           const int bit = __ffs(rest) - 1;
           rest &= rest - 1;
           const int xa = sval(a0, a1, bit), xb = sval(b0, b1, bit), xt = sval(t0, t1, bit);
-          const int C = g.dsize[w * 32 + bit];
-          // every size-dependent region subtracts at most xa + xb + 2 xt from
-          // |e_k|, so sizes beyond that plus theta + 1 all give the same codes
+          int C = (int)((p0 >> bit) & 1u) | ((int)((p1 >> bit) & 1u) << 1) |
+                  ((int)((p2 >> bit) & 1u) << 2) | ((int)((p3 >> bit) & 1u) << 3);
+          if (C >= 15) C = g.dsize[w * 32 + bit];
           const int ce = min(C, xa + xb + 2 * xt + theta + 1);
           if (ce <= kCeff) {
             atomicAdd(&me.table[((xa * 4 + xb) * 4 + xt) * kCeff + ce - 1], 1u);
@@ -423,17 +469,34 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           add_triangle(hist, lut, theta, A, B, C, x, o.y, o.z, o.t, 1);
         }
       }
+      // flush the per-lane counters
 #pragma unroll
-      for (int c = 0; c < kClasses; ++c) {
-        long long v0 = c0[c], v1 = c1[c];
-        for (int d = 16; d; d >>= 1) {
-          v0 += __shfl_xor_sync(0xffffffffu, v0, d);
-          v1 += __shfl_xor_sync(0xffffffffu, v1, d);
-        }
-        if (lane == 0) {
-          const int C = class_rep(c, theta);
-          if (v0) add_triangle(hist, lut, theta, A, B, C, x, 1, 1, 0, v0);
-          if (v1) add_triangle(hist, lut, theta, A, B, C, x, 1, 1, 1, v1);
+      for (int c = 0; c < 18; ++c) {
+        uint32_t v = cnt[c];
+        for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+        cnt[c] = v;
+      }
+      if (lane == 0) {
+        if (kTheta1) {
+          // (xa, xb, xt), first counter, number of sizes
+          const int spec[4][5] = {{0, 0, 1, 0, 4}, {0, 1, 1, 4, 5}, {1, 0, 1, 9, 5}, {1, 1, 0, 14, 4}};
+#pragma unroll
+          for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+              if (c >= spec[s][4]) continue;
+              const uint32_t n = cnt[spec[s][3] + c];
+              if (!n) continue;
+              const int xa = spec[s][0], xb = spec[s][1], xt = spec[s][2];
+              add_triangle(hist, lut, theta, A, B, c + 1, x, xb + xt, xa + xt, xt, (long long)n);
+            }
+        } else {
+#pragma unroll
+          for (int c = 0; c < kClasses; ++c) {
+            const int C = class_rep(c, theta);
+            if (cnt[c]) add_triangle(hist, lut, theta, A, B, C, x, 1, 1, 1, (long long)cnt[c]);
+            if (cnt[5 + c]) add_triangle(hist, lut, theta, A, B, C, x, 1, 1, 0, (long long)cnt[5 + c]);
+          }
         }
       }
       __syncwarp();
@@ -584,6 +647,18 @@ __global__ void k_dense_index(int64_t E, const int64_t* __restrict__ flag,
   }
 }
 
+__global__ void k_dense_keys(int64_t n_dense, const int32_t* __restrict__ drow,
+                             const int64_t* __restrict__ noff, uint32_t* __restrict__ key) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n_dense) key[r] = (uint32_t)(noff[drow[r] + 1] - noff[drow[r]]);
+}
+
+__global__ void k_dense_reindex(int64_t n_dense, const int32_t* __restrict__ drow,
+                                int32_t* __restrict__ didx) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n_dense) didx[drow[r]] = (int32_t)r;
+}
+
 __global__ void k_dense_bits(int64_t n_dense, int64_t W, const int32_t* __restrict__ drow,
                              const int64_t* __restrict__ eoff, const int64_t* __restrict__ noff,
                              const uint2* __restrict__ nadj, const int32_t* __restrict__ didx,
@@ -673,9 +748,13 @@ __global__ void k_size_bits(int64_t n_dense, int64_t W, const int32_t* __restric
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_dense) return;
   const int64_t k = drow[r];
-  dsize[r] = (uint8_t)(eoff[k + 1] - eoff[k]);
-  const int c = size_class((int)(eoff[k + 1] - eoff[k]), theta);
-  atomicOr(&sbits[(int64_t)c * W + (r >> 5)], 1u << (r & 31));
+  const int C = (int)(eoff[k + 1] - eoff[k]);
+  dsize[r] = (uint8_t)C;
+  const int cc = min(C, 15);
+  for (int b = 0; b < 4; ++b)
+    if (cc & (1 << b)) atomicOr(&sbits[(int64_t)b * W + (r >> 5)], 1u << (r & 31));
+  const int c = size_class(C, theta);
+  atomicOr(&sbits[(int64_t)(4 + c) * W + (r >> 5)], 1u << (r & 31));
 }
 
 // stable split of row_order into dense and sparse work orders
@@ -765,7 +844,7 @@ int prepare_split(mochy_ctx* ctx) {
   const size_t b_drow = al((size_t)nd1 * 4);
   const size_t b_dbits = al((size_t)nd1 * 2 * W * 4);
   const size_t b_hidx = al((size_t)std::max<int64_t>(N, 1) * 4);
-  const size_t b_sbits = al((size_t)kClasses * W * 4);
+  const size_t b_sbits = al((size_t)(4 + kClasses) * W * 4);
   const size_t b_ord = al((size_t)std::max<int64_t>(E, 1) * 4);
   const size_t b_dsize = al((size_t)nd1);
   const size_t head = b_didx + b_drow + b_dbits + b_hidx + b_sbits + 2 * b_ord + b_dsize;
@@ -786,8 +865,21 @@ int prepare_split(mochy_ctx* ctx) {
   ctx->split_bytes = head;
   k_dense_index<<<ceil_div(E, 256), 256, 0, st>>>(E, flag, pos, ctx->dense_idx, ctx->dense_row);
   MOCHY_LAUNCHED();
+  // dense indices in ascending line degree (ties by id): triangles among
+  // dense rows are then found from their lowest-degree member
+  if (n_dense > 1) {
+    void* kt;
+    MOCHY_TRY(scratch(ctx, 2, (size_t)n_dense * 4, &kt));
+    k_dense_keys<<<ceil_div(n_dense, 256), 256, 0, st>>>(n_dense, ctx->dense_row, ctx->noff,
+                                                         (uint32_t*)kt);
+    MOCHY_LAUNCHED();
+    MOCHY_TRY(radix_sort_pairs_u32(ctx, (uint32_t*)kt, (uint32_t*)ctx->dense_row, n_dense, 32));
+    k_dense_reindex<<<ceil_div(n_dense, 256), 256, 0, st>>>(n_dense, ctx->dense_row,
+                                                            ctx->dense_idx);
+    MOCHY_LAUNCHED();
+  }
   MOCHY_CUDA(cudaMemsetAsync(ctx->dbits, 0, (size_t)nd1 * 2 * W * 4, st));
-  MOCHY_CUDA(cudaMemsetAsync(ctx->sbits, 0, (size_t)kClasses * W * 4, st));
+  MOCHY_CUDA(cudaMemsetAsync(ctx->sbits, 0, (size_t)(4 + kClasses) * W * 4, st));
   if (n_dense > 0) {
     k_dense_bits<<<(unsigned)std::min<int64_t>(n_dense, 1 << 16), 256, 0, st>>>(
         n_dense, W, ctx->dense_row, ctx->eoff, ctx->noff, ctx->nadj, ctx->dense_idx, ctx->dbits);
@@ -863,9 +955,46 @@ int prepare_split(mochy_ctx* ctx) {
   return MOCHY_OK;
 }
 
+// Phase timing for MOCHY_TRACE=1: events around each kernel, printed to
+// stderr after the call.
+struct PhaseTimer {
+  bool on = false;
+  cudaStream_t st;
+  cudaEvent_t ev[8];
+  const char* name[8];
+  int n = 0;
+  explicit PhaseTimer(cudaStream_t s) : st(s) {
+    const char* e = getenv("MOCHY_TRACE");
+    on = e && e[0] && e[0] != '0';
+  }
+  void mark(const char* what) {
+    if (!on || n >= 8) return;
+    cudaEventCreate(&ev[n]);
+    cudaEventRecord(ev[n], st);
+    name[n++] = what;
+  }
+  void report(const mochy_ctx* c) {
+    if (!on || n < 2) return;
+    cudaEventSynchronize(ev[n - 1]);
+    fprintf(stderr, "[mochy] split exact: E=%lld dense=%lld (threshold %d, %lld words) heavy=%lld\n",
+            (long long)c->n_edges, (long long)c->n_dense, c->dense_thr_used,
+            (long long)c->wwords, (long long)c->n_heavy);
+    for (int i = 1; i < n; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+      fprintf(stderr, "[mochy]   %-18s %10.3f ms\n", name[i], ms);
+    }
+    for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
+    n = 0;
+  }
+};
+
 int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
   cudaStream_t st = ctx->stream;
+  PhaseTimer timer(st);
+  timer.mark("start");
   MOCHY_TRY(prepare_split(ctx));
+  timer.mark("prepare");
   SplitArgs g;
   g.n_edges = ctx->n_edges;
   g.eoff = ctx->eoff;
@@ -888,6 +1017,7 @@ int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
   g.dvoff = ctx->dvoff;
   g.dvedge = ctx->dvedge;
   g.dsize = ctx->dsize;
+  g.cbits = ctx->sbits + 4 * ctx->wwords;
   MOCHY_CUDA(cudaMemsetAsync(ctx->counters, 0, 16 * sizeof(int32_t), st));
   // open pairs
   {
@@ -900,6 +1030,7 @@ int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
       k_open_pairs<<<grid, kOpenThreads, 0, st>>>(g);
       MOCHY_LAUNCHED();
     }
+    timer.mark("open pairs");
   }
   // triangles from sparse rows
   if (ctx->n_sparse > 0) {
@@ -919,23 +1050,25 @@ int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
                                                       ctx->n_sparse);
     k_sparse_triangles<<<grid, kThreads, smem, st>>>(g, std::max(max_deg, 1));
     MOCHY_LAUNCHED();
+    timer.mark("sparse triangles");
   }
   // triangles of dense rows
   if (ctx->n_dense > 0) {
     const size_t smem = dense_smem_bytes(ctx->wwords);
-    MOCHY_CUDA(cudaFuncSetAttribute(k_dense_triangles,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = ctx->theta == 1 ? k_dense_triangles<true> : k_dense_triangles<false>;
+    MOCHY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_triangles, kDThreads,
-                                                             smem));
+    MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDThreads, smem));
     g.order = ctx->dense_order;
     g.n_order = ctx->n_dense;
     g.queue = ctx->counters + 6;
     const unsigned grid = (unsigned)std::min<int64_t>((int64_t)ctx->num_sms * std::max(per_sm, 1),
                                                       ctx->n_dense);
-    k_dense_triangles<<<grid, kDThreads, smem, st>>>(g);
+    kern<<<grid, kDThreads, smem, st>>>(g);
     MOCHY_LAUNCHED();
+    timer.mark("dense triangles");
   }
+  timer.report(ctx);
   return MOCHY_OK;
 }
 
