@@ -28,7 +28,7 @@ EXPORTS = [
     "mochy_get_hypergraph", "mochy_project", "mochy_line_degrees", "mochy_count_exact",
     "mochy_count_exact_subset", "mochy_count_sampled", "mochy_randomize", "mochy_profile",
     "mochy_motif_pattern", "mochy_stream", "mochy_device_bytes", "mochy_kernel_launches",
-    "mochy_strerror", "mochy_last_error",
+    "mochy_strerror", "mochy_last_error", "mochy_trace", "mochy_trace_read",
 ]
 
 
@@ -85,6 +85,8 @@ def load_library(path: str = LIB_PATH):
                                             ctypes.POINTER(vp)]
             lib.mochy_profile.argtypes = [vp, i32, ctypes.c_uint64, vp, vp, vp, vp, vp, vp]
             lib.mochy_motif_pattern.argtypes = [ctypes.c_int, i32, vp]
+            lib.mochy_trace.argtypes = [vp, ctypes.c_int]
+            lib.mochy_trace_read.argtypes = [vp, ctypes.c_char_p, i64]
             _lib = lib
     return _lib
 
@@ -219,6 +221,17 @@ def mochy_stream(ctx: int) -> int:
 
 def mochy_device_bytes(ctx: int) -> int:
     return int(load_library().mochy_device_bytes(ctx))
+
+
+def mochy_trace(ctx: int, enable: bool) -> None:
+    _check(load_library().mochy_trace(ctx, 1 if enable else 0), "mochy_trace")
+
+
+def mochy_trace_read(ctx: int) -> dict:
+    import json
+    buf = ctypes.create_string_buffer(4096)
+    _check(load_library().mochy_trace_read(ctx, buf, 4096), "mochy_trace_read")
+    return json.loads(buf.value.decode())
 
 
 def mochy_kernel_launches() -> int:

@@ -183,6 +183,7 @@ int mochy_create(mochy_ctx** out, const mochy_config* cfg_in) {
   ctx->budget = cfg.hbm_budget_bytes;
   ctx->exact_kernel = cfg.exact_kernel;
   ctx->dense_thr = cfg.dense_threshold;
+  memset(ctx->last_stats, 0, sizeof(ctx->last_stats));
   int rc = MOCHY_OK;
   auto bail = [&](int code) {
     mochy_destroy(ctx);
@@ -229,6 +230,7 @@ int mochy_destroy(mochy_ctx* ctx) {
     b.bytes = 0;
   }
   if (ctx->hist) cudaFree(ctx->hist);
+  if (ctx->stats) cudaFree(ctx->stats);
   if (ctx->tables.lut3) cudaFree(ctx->tables.lut3);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -485,6 +487,35 @@ int mochy_motif_pattern(int kind, int32_t id, uint8_t* regions_out) {
 }
 
 void* mochy_stream(mochy_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+int mochy_trace(mochy_ctx* ctx, int enable) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  ctx->trace = enable != 0;
+  return MOCHY_OK;
+}
+
+int mochy_trace_read(mochy_ctx* ctx, char* buf, int64_t len) {
+  if (!ctx || !buf || len <= 0) return fail(MOCHY_E_INVALID, "bad argument");
+  std::string js = "{\"phases_ms\": {";
+  for (int i = 0; i < ctx->n_phases; ++i) {
+    char item[96];
+    snprintf(item, sizeof(item), "%s\"%s\": %.6f", i ? ", " : "", ctx->phase_name[i],
+             ctx->phase_ms[i]);
+    js += item;
+  }
+  char tail[512];
+  snprintf(tail, sizeof(tail),
+           "}, \"dense_rows\": %lld, \"dense_threshold\": %d, \"dense_words\": %lld, "
+           "\"heavy_nodes\": %lld, \"words_scanned\": %llu, \"candidates\": %llu, "
+           "\"table_candidates\": %llu, \"exact_candidates\": %llu, \"light_corrections\": %llu}",
+           (long long)ctx->n_dense, ctx->dense_thr_used, (long long)ctx->wwords,
+           (long long)ctx->n_heavy, ctx->last_stats[0], ctx->last_stats[1], ctx->last_stats[2],
+           ctx->last_stats[3], ctx->last_stats[4]);
+  js += tail;
+  if ((int64_t)js.size() + 1 > len) return fail(MOCHY_E_INVALID, "buffer too small");
+  memcpy(buf, js.c_str(), js.size() + 1);
+  return MOCHY_OK;
+}
 
 int64_t mochy_device_bytes(mochy_ctx* ctx) { return ctx ? ctx->held : 0; }
 

@@ -128,6 +128,15 @@ struct mochy_ctx {
 
   // pinned host staging
   void* pinned = nullptr;
+
+  // tracing: per-phase durations of the last traced call (CUDA events on the
+  // context's stream) and kernel statistics
+  bool trace = false;
+  int n_phases = 0;
+  char phase_name[8][24];
+  double phase_ms[8];
+  unsigned long long* stats = nullptr;   // [8] device counters, when tracing
+  unsigned long long last_stats[8];
 };
 
 namespace mochy {

@@ -104,6 +104,7 @@ struct SplitArgs {
   const int32_t* dvedge;
   const uint8_t* dsize;
   const uint32_t* cbits;     // [5][W] size classes (theta other than 1)
+  unsigned long long* stats; // tracing counters or null
   const int32_t* order;
   int64_t n_order;
   int32_t* queue;
@@ -376,6 +377,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       uint32_t cnt[18];
 #pragma unroll
       for (int c = 0; c < 18; ++c) cnt[c] = 0u;
+      unsigned long long st_cand = 0, st_table = 0, st_exact = 0, st_light = 0;
       const int64_t first = (int64_t)(bd + 1);
       const int64_t fw = first >> 5;
       for (int64_t w = fw + lane; w < W; w += 32) {
@@ -416,6 +418,11 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
             cnt[c] += __popc(s001 & sc);
             cnt[5 + c] += __popc(s110 & sc);
           }
+        }
+        if (g.stats) {
+          st_cand += __popc(m);
+          st_table += __popc(valid & ~done);
+          st_exact += __popc(ovf);
         }
         uint32_t rest = valid & ~done;
         while (rest) {
@@ -461,12 +468,28 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           for (int l2 = 0; l2 < l && !seen; ++l2) seen = has_node(g.enode + kb, C, me.light[l2]);
           if (seen) continue;
           const Overlap o = overlaps(anodes, A, me.bnodes, B, g.enode + kb, C, g.heavy_idx);
+          if (g.stats) ++st_light;
           const bool hovf = o.hz - o.ht > 3 || o.hy - o.ht > 3 || o.ht > 3;
           if (!hovf && o.hz >= 1 && o.hy >= 1) {
             // counted by the word loop with the heavy-node overlaps
             add_triangle(hist, lut, theta, A, B, C, x, o.hy, o.hz, o.ht, -1);
           }
           add_triangle(hist, lut, theta, A, B, C, x, o.y, o.z, o.t, 1);
+        }
+      }
+      if (g.stats) {
+        for (int d = 16; d; d >>= 1) {
+          st_cand += __shfl_xor_sync(0xffffffffu, st_cand, d);
+          st_table += __shfl_xor_sync(0xffffffffu, st_table, d);
+          st_exact += __shfl_xor_sync(0xffffffffu, st_exact, d);
+          st_light += __shfl_xor_sync(0xffffffffu, st_light, d);
+        }
+        if (lane == 0) {
+          atomicAdd(&g.stats[0], (unsigned long long)(W - fw));
+          atomicAdd(&g.stats[1], st_cand);
+          atomicAdd(&g.stats[2], st_table);
+          atomicAdd(&g.stats[3], st_exact);
+          atomicAdd(&g.stats[4], st_light);
         }
       }
       // flush the per-lane counters
@@ -955,17 +978,19 @@ int prepare_split(mochy_ctx* ctx) {
   return MOCHY_OK;
 }
 
-// Phase timing for MOCHY_TRACE=1: events around each kernel, printed to
-// stderr after the call.
+// Phase timing when tracing is on (mochy_trace or MOCHY_TRACE=1): events
+// around each kernel on the context's stream, kept in the context and, with
+// MOCHY_TRACE set, printed to stderr.
 struct PhaseTimer {
-  bool on = false;
+  bool on = false, print = false;
   cudaStream_t st;
   cudaEvent_t ev[8];
   const char* name[8];
   int n = 0;
-  explicit PhaseTimer(cudaStream_t s) : st(s) {
+  PhaseTimer(const mochy_ctx* c) : st(c->stream) {
     const char* e = getenv("MOCHY_TRACE");
-    on = e && e[0] && e[0] != '0';
+    print = e && e[0] && e[0] != '0';
+    on = c->trace || print;
   }
   void mark(const char* what) {
     if (!on || n >= 8) return;
@@ -973,16 +998,28 @@ struct PhaseTimer {
     cudaEventRecord(ev[n], st);
     name[n++] = what;
   }
-  void report(const mochy_ctx* c) {
+  void report(mochy_ctx* c) {
     if (!on || n < 2) return;
     cudaEventSynchronize(ev[n - 1]);
-    fprintf(stderr, "[mochy] split exact: E=%lld dense=%lld (threshold %d, %lld words) heavy=%lld\n",
-            (long long)c->n_edges, (long long)c->n_dense, c->dense_thr_used,
-            (long long)c->wwords, (long long)c->n_heavy);
+    c->n_phases = 0;
     for (int i = 1; i < n; ++i) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
-      fprintf(stderr, "[mochy]   %-18s %10.3f ms\n", name[i], ms);
+      snprintf(c->phase_name[c->n_phases], sizeof(c->phase_name[0]), "%s", name[i]);
+      c->phase_ms[c->n_phases++] = ms;
+    }
+    if (c->stats)
+      cudaMemcpy(c->last_stats, c->stats, sizeof(c->last_stats), cudaMemcpyDeviceToHost);
+    if (print) {
+      fprintf(stderr, "[mochy] split exact: E=%lld dense=%lld (threshold %d, %lld words) heavy=%lld\n",
+              (long long)c->n_edges, (long long)c->n_dense, c->dense_thr_used,
+              (long long)c->wwords, (long long)c->n_heavy);
+      for (int i = 0; i < c->n_phases; ++i)
+        fprintf(stderr, "[mochy]   %-18s %10.3f ms\n", c->phase_name[i], c->phase_ms[i]);
+      if (c->stats)
+        fprintf(stderr, "[mochy]   words %llu  candidates %llu  table %llu  exact %llu  light %llu\n",
+                c->last_stats[0], c->last_stats[1], c->last_stats[2], c->last_stats[3],
+                c->last_stats[4]);
     }
     for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
     n = 0;
@@ -991,11 +1028,17 @@ struct PhaseTimer {
 
 int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
   cudaStream_t st = ctx->stream;
-  PhaseTimer timer(st);
+  SplitArgs g;
+  PhaseTimer timer(ctx);
+  if (timer.on && !ctx->stats) {
+    void* p;
+    MOCHY_TRY(dev_alloc(ctx, &p, 8 * sizeof(unsigned long long)));
+    ctx->stats = (unsigned long long*)p;
+  }
+  if (ctx->stats) MOCHY_CUDA(cudaMemsetAsync(ctx->stats, 0, 8 * sizeof(unsigned long long), st));
   timer.mark("start");
   MOCHY_TRY(prepare_split(ctx));
   timer.mark("prepare");
-  SplitArgs g;
   g.n_edges = ctx->n_edges;
   g.eoff = ctx->eoff;
   g.enode = ctx->enode;
@@ -1018,6 +1061,7 @@ int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
   g.dvedge = ctx->dvedge;
   g.dsize = ctx->dsize;
   g.cbits = ctx->sbits + 4 * ctx->wwords;
+  g.stats = timer.on ? ctx->stats : nullptr;
   MOCHY_CUDA(cudaMemsetAsync(ctx->counters, 0, 16 * sizeof(int32_t), st));
   // open pairs
   {
