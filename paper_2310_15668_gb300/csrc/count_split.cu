@@ -249,6 +249,31 @@ __device__ __forceinline__ void slice_add(uint32_t& c0, uint32_t& c1, uint32_t& 
   c1 ^= k0;
 }
 
+// lanes (bits) whose 2-bit sliced value equals v
+__device__ __forceinline__ uint32_t eq2(uint32_t c0, uint32_t c1, int v) {
+  return ((v & 1) ? c0 : ~c0) & ((v & 2) ? c1 : ~c1);
+}
+
+// bits whose 4-bit value (planes p0..p3) equals / is at least k
+__device__ __forceinline__ uint32_t eq4(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3, int k) {
+  return ((k & 1) ? p0 : ~p0) & ((k & 2) ? p1 : ~p1) & ((k & 4) ? p2 : ~p2) & ((k & 8) ? p3 : ~p3);
+}
+
+__device__ __forceinline__ uint32_t ge4(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3, int k) {
+  const uint32_t pl[4] = {p0, p1, p2, p3};
+  uint32_t gt = 0u, eq = 0xffffffffu;
+#pragma unroll
+  for (int b = 3; b >= 0; --b) {
+    if ((k >> b) & 1) {
+      eq &= pl[b];
+    } else {
+      gt |= eq & pl[b];
+      eq &= ~pl[b];
+    }
+  }
+  return gt | eq;
+}
+
 __device__ __forceinline__ int sval(uint32_t c0, uint32_t c1, int bit) {
   return (int)((c0 >> bit) & 1u) + 2 * (int)((c1 >> bit) & 1u);
 }
@@ -424,19 +449,33 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           st_table += __popc(valid & ~done);
           st_exact += __popc(ovf);
         }
+        // remaining candidates, one group of equal (xa, xb, xt, effective
+        // size) at a time: the group's mask is built bit-parallel
         uint32_t rest = valid & ~done;
         while (rest) {
           const int bit = __ffs(rest) - 1;
-          rest &= rest - 1;
           const int xa = sval(a0, a1, bit), xb = sval(b0, b1, bit), xt = sval(t0, t1, bit);
-          int C = (int)((p0 >> bit) & 1u) | ((int)((p1 >> bit) & 1u) << 1) |
-                  ((int)((p2 >> bit) & 1u) << 2) | ((int)((p3 >> bit) & 1u) << 3);
-          if (C >= 15) C = g.dsize[w * 32 + bit];
-          const int ce = min(C, xa + xb + 2 * xt + theta + 1);
-          if (ce <= kCeff) {
-            atomicAdd(&me.table[((xa * 4 + xb) * 4 + xt) * kCeff + ce - 1], 1u);
+          const uint32_t same = rest & eq2(a0, a1, xa) & eq2(b0, b1, xb) & eq2(t0, t1, xt);
+          const int C4 = (int)((p0 >> bit) & 1u) | ((int)((p1 >> bit) & 1u) << 1) |
+                         ((int)((p2 >> bit) & 1u) << 2) | ((int)((p3 >> bit) & 1u) << 3);
+          const int bound = xa + xb + 2 * xt + theta + 1;
+          uint32_t grp;
+          int ce;
+          if (C4 >= bound && bound <= 15) {
+            grp = same & ge4(p0, p1, p2, p3, bound);       // all sizes >= bound
+            ce = bound;
+          } else if (C4 < 15) {
+            grp = same & eq4(p0, p1, p2, p3, C4);          // this exact size
+            ce = C4;
           } else {
-            add_triangle(hist, lut, theta, A, B, C, x, xb + xt, xa + xt, xt, 1);
+            grp = 1u << bit;                               // size >= 15: exact lookup
+            ce = min((int)g.dsize[w * 32 + bit], bound);
+          }
+          rest &= ~grp;
+          if (ce <= kCeff) {
+            atomicAdd(&me.table[((xa * 4 + xb) * 4 + xt) * kCeff + ce - 1], (uint32_t)__popc(grp));
+          } else {
+            add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, __popc(grp));
           }
         }
         uint32_t e = ovf;
@@ -492,34 +531,25 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           atomicAdd(&g.stats[4], st_light);
         }
       }
-      // flush the per-lane counters
+      // flush the per-lane counters: lane c handles counter c
+      uint32_t mine = 0u;
 #pragma unroll
       for (int c = 0; c < 18; ++c) {
-        uint32_t v = cnt[c];
-        for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-        cnt[c] = v;
+        const uint32_t v = __reduce_add_sync(0xffffffffu, cnt[c]);
+        if (lane == c) mine = v;
       }
-      if (lane == 0) {
+      if (mine) {
         if (kTheta1) {
-          // (xa, xb, xt), first counter, number of sizes
-          const int spec[4][5] = {{0, 0, 1, 0, 4}, {0, 1, 1, 4, 5}, {1, 0, 1, 9, 5}, {1, 1, 0, 14, 4}};
-#pragma unroll
-          for (int s = 0; s < 4; ++s)
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-              if (c >= spec[s][4]) continue;
-              const uint32_t n = cnt[spec[s][3] + c];
-              if (!n) continue;
-              const int xa = spec[s][0], xb = spec[s][1], xt = spec[s][2];
-              add_triangle(hist, lut, theta, A, B, c + 1, x, xb + xt, xa + xt, xt, (long long)n);
-            }
-        } else {
-#pragma unroll
-          for (int c = 0; c < kClasses; ++c) {
-            const int C = class_rep(c, theta);
-            if (cnt[c]) add_triangle(hist, lut, theta, A, B, C, x, 1, 1, 1, (long long)cnt[c]);
-            if (cnt[5 + c]) add_triangle(hist, lut, theta, A, B, C, x, 1, 1, 0, (long long)cnt[5 + c]);
-          }
+          // counters 0-3: (0,0,1) sizes 1..4+; 4-8: (0,1,1) 1..5+; 9-13: (1,0,1)
+          // 1..5+; 14-17: (1,1,0) 1..4+
+          const int s = lane < 4 ? 0 : lane < 9 ? 1 : lane < 14 ? 2 : 3;
+          const int c = lane - (s == 0 ? 0 : s == 1 ? 4 : s == 2 ? 9 : 14);
+          const int xa = s == 2 || s == 3 ? 1 : 0, xb = s == 1 || s == 3 ? 1 : 0,
+                    xt = s == 3 ? 0 : 1;
+          add_triangle(hist, lut, theta, A, B, c + 1, x, xb + xt, xa + xt, xt, (long long)mine);
+        } else if (lane < 2 * kClasses) {
+          const int C = class_rep(lane % kClasses, theta);
+          add_triangle(hist, lut, theta, A, B, C, x, 1, 1, lane < kClasses ? 1 : 0, (long long)mine);
         }
       }
       __syncwarp();
