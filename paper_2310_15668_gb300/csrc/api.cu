@@ -507,10 +507,12 @@ int mochy_trace_read(mochy_ctx* ctx, char* buf, int64_t len) {
   snprintf(tail, sizeof(tail),
            "}, \"dense_rows\": %lld, \"dense_threshold\": %d, \"dense_words\": %lld, "
            "\"heavy_nodes\": %lld, \"words_scanned\": %llu, \"candidates\": %llu, "
-           "\"table_candidates\": %llu, \"exact_candidates\": %llu, \"light_corrections\": %llu}",
+           "\"table_candidates\": %llu, \"exact_candidates\": %llu, \"light_corrections\": %llu, "
+           "\"clk_setup\": %llu, \"clk_words\": %llu, \"clk_finish\": %llu}",
            (long long)ctx->n_dense, ctx->dense_thr_used, (long long)ctx->wwords,
            (long long)ctx->n_heavy, ctx->last_stats[0], ctx->last_stats[1], ctx->last_stats[2],
-           ctx->last_stats[3], ctx->last_stats[4]);
+           ctx->last_stats[3], ctx->last_stats[4], ctx->last_stats[5], ctx->last_stats[6],
+           ctx->last_stats[7]);
   js += tail;
   if ((int64_t)js.size() + 1 > len) return fail(MOCHY_E_INVALID, "buffer too small");
   memcpy(buf, js.c_str(), js.size() + 1);

@@ -240,6 +240,7 @@ struct WarpScratch {
   int32_t lgrp[128];     // their group (0 A, 1 B, 2 T)
   int32_t n[5];          // nA, nB, nT, nlight, pad
   uint32_t table[kCombo * kCeff];
+  uint32_t dirty[kCombo * kCeff / 32];
 };
 
 __device__ __forceinline__ void slice_add(uint32_t& c0, uint32_t& c1, uint32_t& ovf, uint32_t m) {
@@ -330,6 +331,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
   WarpScratch& me = ws[warp];
   load_lut(lut, g.lut3, hist);
   for (int q = lane; q < kCombo * kCeff; q += 32) me.table[q] = 0u;
+  me.dirty[lane] = 0u;
   const int theta = g.theta;
   const uint32_t* P0 = g.sbits;
   const uint32_t* P1 = g.sbits + W;
@@ -358,6 +360,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       const int64_t b = ent_id(eab);
       const int bd = g.dense_idx[b];
       if (bd <= ad) continue;                       // b must be dense and after a
+      const long long t_setup0 = g.stats ? clock64() : 0;
       const int B = ent_size(eab);
       const int x = entry_omega(eab.y, A);
       if (lane < B) me.bnodes[lane] = g.enode[g.eoff[b] + lane];
@@ -405,10 +408,14 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       unsigned long long st_cand = 0, st_table = 0, st_exact = 0, st_light = 0;
       const int64_t first = (int64_t)(bd + 1);
       const int64_t fw = first >> 5;
-      for (int64_t w = fw + lane; w < W; w += 32) {
-        uint32_t m = A1[w] & __ldg(&B1[w]);
+      long long t_words0 = g.stats ? clock64() : 0;
+      // uniform loop: every lane runs every iteration (lanes past the end see
+      // an empty word), so the warp stays converged
+      for (int64_t w0 = fw; w0 < W; w0 += 32) {
+        const bool inr = w0 + lane < W;
+        const int64_t w = inr ? w0 + lane : W - 1;
+        uint32_t m = inr ? (A1[w] & __ldg(&B1[w])) : 0u;
         if (w == fw) m &= 0xffffffffu << (first & 31);
-        if (!m) continue;
         uint32_t a0 = 0, a1 = 0, b0 = 0, b1 = 0, t0 = 0, t1 = 0, ovf = 0;
         for (int h = 0; h < nA; ++h) slice_add(a0, a1, ovf, __ldg(&g.nbits[(int64_t)me.hidx[0][h] * W + w]));
         for (int h = 0; h < nB; ++h) slice_add(b0, b1, ovf, __ldg(&g.nbits[(int64_t)me.hidx[1][h] * W + w]));
@@ -452,7 +459,8 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         // remaining candidates, one group of equal (xa, xb, xt, effective
         // size) at a time: the group's mask is built bit-parallel
         uint32_t rest = valid & ~done;
-        while (rest) {
+        while (__any_sync(0xffffffffu, rest != 0u)) {
+          if (!rest) continue;
           const int bit = __ffs(rest) - 1;
           const int xa = sval(a0, a1, bit), xb = sval(b0, b1, bit), xt = sval(t0, t1, bit);
           const uint32_t same = rest & eq2(a0, a1, xa) & eq2(b0, b1, xb) & eq2(t0, t1, xt);
@@ -473,13 +481,16 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           }
           rest &= ~grp;
           if (ce <= kCeff) {
-            atomicAdd(&me.table[((xa * 4 + xb) * 4 + xt) * kCeff + ce - 1], (uint32_t)__popc(grp));
+            const int key = ((xa * 4 + xb) * 4 + xt) * kCeff + ce - 1;
+            atomicAdd(&me.table[key], (uint32_t)__popc(grp));
+            atomicOr(&me.dirty[key >> 5], 1u << (key & 31));
           } else {
             add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, __popc(grp));
           }
         }
         uint32_t e = ovf;
-        while (e) {
+        while (__any_sync(0xffffffffu, e != 0u)) {
+          if (!e) continue;
           const int bit = __ffs(e) - 1;
           e &= e - 1;
           const int64_t k = g.dense_row[w * 32 + bit];
@@ -490,6 +501,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           add_triangle(hist, lut, theta, A, B, C, x, o.y, o.z, o.t, 1);
         }
       }
+      long long t_words1 = g.stats ? clock64() : 0;
       // candidates holding a light node: replace the word loop's class by the
       // exact one (each candidate once: it is handled at its first light node)
       for (int l = 0; l < nL; ++l) {
@@ -553,13 +565,25 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         }
       }
       __syncwarp();
-      for (int q = lane; q < kCombo * kCeff; q += 32) {
-        const uint32_t n = me.table[q];
-        if (!n) continue;
-        me.table[q] = 0u;
-        const int ce = q % kCeff + 1, combo = q / kCeff;
-        const int xt = combo & 3, xb = (combo >> 2) & 3, xa = combo >> 4;
-        add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, (long long)n);
+      {
+        uint32_t dw = me.dirty[lane];
+        me.dirty[lane] = 0u;
+        while (dw) {
+          const int q = lane * 32 + __ffs(dw) - 1;
+          dw &= dw - 1;
+          const uint32_t n = me.table[q];
+          me.table[q] = 0u;
+          if (!n) continue;
+          const int ce = q % kCeff + 1, combo = q / kCeff;
+          const int xt = combo & 3, xb = (combo >> 2) & 3, xa = combo >> 4;
+          add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, (long long)n);
+        }
+      }
+      if (g.stats && lane == 0) {
+        const long long t_end = clock64();
+        atomicAdd(&g.stats[5], (unsigned long long)(t_words0 - t_setup0));
+        atomicAdd(&g.stats[6], (unsigned long long)(t_words1 - t_words0));
+        atomicAdd(&g.stats[7], (unsigned long long)(t_end - t_words1));
       }
       __syncwarp();
     }

@@ -11,7 +11,9 @@
 //                 rows, f_d = S_d / S the chance that a neighbour is dense
 //                 and W = n_dense / 32 words;
 //   sparse part ~ sum over sparse rows of deg^2 (pairs of neighbours probed).
-// The relative weight of a word to a probe was measured on GB300 (about 2).
+// The dense term overestimates the words scanned about twofold (dense rows
+// are ordered by degree), and a scanned word and a probed pair cost about
+// the same on GB300, so the word term gets weight 0.5.
 #include <cmath>
 #include <vector>
 
@@ -34,7 +36,7 @@ int choose_dense_threshold(mochy_ctx* ctx) {
     deg[i] = off[i + 1] - off[i];
     S += (double)deg[i];
   }
-  const double word_weight = 2.0;
+  const double word_weight = 0.5;
   int best = -1;
   double best_cost = 0.0;
   for (int64_t thr = 32; thr <= (int64_t)1 << 20; thr <<= 1) {
