@@ -234,11 +234,14 @@ constexpr int kCeff = 16;          // effective sizes kept in the table
 constexpr int kCombo = 64;         // (xa, xb, xt), 2 bits each
 
 struct WarpScratch {
+  int64_t lpos[128];     // next unread entry of each light node's dense list
+  int64_t lend[128];     // end of that list
+  int32_t lnext[128];    // dense index at lpos (INT_MAX when done)
   int32_t bnodes[64];
   int32_t hidx[3][64];   // heavy indices of groups A, B, T
   int32_t light[128];    // light nodes of e_a | e_b
   int32_t lgrp[128];     // their group (0 A, 1 B, 2 T)
-  int32_t n[5];          // nA, nB, nT, nlight, pad
+  int32_t n[6];          // nA, nB, nT, nlight, pad
   uint32_t table[kCombo * kCeff];
   uint32_t dirty[kCombo * kCeff / 32];
 };
@@ -327,6 +330,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
   uint32_t* A1 = (uint32_t*)(ws + kDWarps);
   const int64_t W = g.wwords;
   __shared__ int64_t slot_s;
+  __shared__ int64_t row_next;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpScratch& me = ws[warp];
   load_lut(lut, g.lut3, hist);
@@ -355,7 +359,13 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       if (kd >= 0) atomicOr(&A1[kd >> 5], 1u << (kd & 31));
     }
     __syncthreads();
-    for (int64_t idx = rb + warp; idx < re; idx += kDWarps) {
+    if (threadIdx.x == 0) row_next = rb;
+    __syncthreads();
+    while (true) {
+      int64_t idx = 0;
+      if (lane == 0) idx = atomicAdd((unsigned long long*)&row_next, 1ull);
+      idx = __shfl_sync(0xffffffffu, idx, 0);
+      if (idx >= re) break;
       const uint2 eab = g.nadj[idx];
       const int64_t b = ent_id(eab);
       const int bd = g.dense_idx[b];
@@ -393,6 +403,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         if (lt) {
           const int pos = me.n[3] + __popc(bal & ((1u << lane) - 1u));
           me.light[pos] = u;
+          me.lgrp[pos] = grp;
         }
         __syncwarp();
         if (lane == 0) me.n[3] += __popc(bal);
@@ -408,6 +419,21 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       unsigned long long st_cand = 0, st_table = 0, st_exact = 0, st_light = 0;
       const int64_t first = (int64_t)(bd + 1);
       const int64_t fw = first >> 5;
+      // light nodes: cursors into their dense lists (fewer than 32 entries
+      // each), skipping dense indices before `first`
+      for (int l = 0; l < nL; ++l) {
+        const int32_t v = me.light[l];
+        const int64_t lb = g.dvoff[v], le = g.dvoff[v + 1];
+        const int32_t e = lb + lane < le ? g.dvedge[lb + lane] : 0x7fffffff;
+        const int before = __popc(__ballot_sync(0xffffffffu, e < first));
+        const int32_t nx = __shfl_sync(0xffffffffu, e, before & 31);
+        if (lane == 0) {
+          me.lpos[l] = lb + before;
+          me.lend[l] = le;
+          me.lnext[l] = lb + before < le ? nx : 0x7fffffff;
+        }
+      }
+      __syncwarp();
       long long t_words0 = g.stats ? clock64() : 0;
       // uniform loop: every lane runs every iteration (lanes past the end see
       // an empty word), so the warp stays converged
@@ -420,6 +446,32 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         for (int h = 0; h < nA; ++h) slice_add(a0, a1, ovf, __ldg(&g.nbits[(int64_t)me.hidx[0][h] * W + w]));
         for (int h = 0; h < nB; ++h) slice_add(b0, b1, ovf, __ldg(&g.nbits[(int64_t)me.hidx[1][h] * W + w]));
         for (int h = 0; h < nT; ++h) slice_add(t0, t1, ovf, __ldg(&g.nbits[(int64_t)me.hidx[2][h] * W + w]));
+        // light nodes with a dense index in this iteration's 32 words
+        const int64_t hi64 = (w0 + 32) * 32;
+        const int32_t hi = hi64 < 0x7fffffff ? (int32_t)hi64 : 0x7fffffff;
+        for (int l = 0; l < nL; ++l) {
+          if (me.lnext[l] >= hi) continue;              // uniform: same value on all lanes
+          const int64_t pos = me.lpos[l], le = me.lend[l];
+          const int32_t e = pos + lane < le ? g.dvedge[pos + lane] : 0x7fffffff;
+          const int nin = __popc(__ballot_sync(0xffffffffu, e < hi));
+          const int grp = me.lgrp[l];
+          for (int j = 0; j < nin; ++j) {
+            const int32_t kd = __shfl_sync(0xffffffffu, e, j);
+            if ((int64_t)(kd >> 5) == w && inr) {
+              const uint32_t bitm = 1u << (kd & 31);
+              if (grp == 0) slice_add(a0, a1, ovf, bitm);
+              else if (grp == 1) slice_add(b0, b1, ovf, bitm);
+              else slice_add(t0, t1, ovf, bitm);
+            }
+          }
+          const int32_t nx = __shfl_sync(0xffffffffu, e, nin & 31);
+          __syncwarp();
+          if (lane == 0) {
+            me.lpos[l] = pos + nin;
+            me.lnext[l] = pos + nin < le ? nx : 0x7fffffff;
+          }
+          __syncwarp();
+        }
         const uint32_t za = a0 | a1, zb = b0 | b1, zt = t0 | t1;
         ovf &= m;
         const uint32_t valid = m & (za | zt) & (zb | zt) & ~ovf;
@@ -497,52 +549,10 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           const int64_t kb = g.eoff[k];
           const int C = (int)(g.eoff[k + 1] - kb);
           const Overlap o = overlaps(anodes, A, me.bnodes, B, g.enode + kb, C, g.heavy_idx);
-          if (o.z != o.hz || o.y != o.hy) continue;   // light-touched: handled below
           add_triangle(hist, lut, theta, A, B, C, x, o.y, o.z, o.t, 1);
         }
       }
       long long t_words1 = g.stats ? clock64() : 0;
-      // candidates holding a light node: replace the word loop's class by the
-      // exact one (each candidate once: it is handled at its first light node)
-      for (int l = 0; l < nL; ++l) {
-        const int32_t v = me.light[l];
-        for (int64_t q = g.dvoff[v] + lane; q < g.dvoff[v + 1]; q += 32) {
-          const int kd = g.dvedge[q];
-          if (kd <= bd) continue;
-          const int w = kd >> 5;
-          const uint32_t bit = 1u << (kd & 31);
-          if (!(A1[w] & __ldg(&B1[w]) & bit)) continue;
-          const int64_t k = g.dense_row[kd];
-          const int64_t kb = g.eoff[k];
-          const int C = (int)(g.eoff[k + 1] - kb);
-          bool seen = false;
-          for (int l2 = 0; l2 < l && !seen; ++l2) seen = has_node(g.enode + kb, C, me.light[l2]);
-          if (seen) continue;
-          const Overlap o = overlaps(anodes, A, me.bnodes, B, g.enode + kb, C, g.heavy_idx);
-          if (g.stats) ++st_light;
-          const bool hovf = o.hz - o.ht > 3 || o.hy - o.ht > 3 || o.ht > 3;
-          if (!hovf && o.hz >= 1 && o.hy >= 1) {
-            // counted by the word loop with the heavy-node overlaps
-            add_triangle(hist, lut, theta, A, B, C, x, o.hy, o.hz, o.ht, -1);
-          }
-          add_triangle(hist, lut, theta, A, B, C, x, o.y, o.z, o.t, 1);
-        }
-      }
-      if (g.stats) {
-        for (int d = 16; d; d >>= 1) {
-          st_cand += __shfl_xor_sync(0xffffffffu, st_cand, d);
-          st_table += __shfl_xor_sync(0xffffffffu, st_table, d);
-          st_exact += __shfl_xor_sync(0xffffffffu, st_exact, d);
-          st_light += __shfl_xor_sync(0xffffffffu, st_light, d);
-        }
-        if (lane == 0) {
-          atomicAdd(&g.stats[0], (unsigned long long)(W - fw));
-          atomicAdd(&g.stats[1], st_cand);
-          atomicAdd(&g.stats[2], st_table);
-          atomicAdd(&g.stats[3], st_exact);
-          atomicAdd(&g.stats[4], st_light);
-        }
-      }
       // flush the per-lane counters: lane c handles counter c
       uint32_t mine = 0u;
 #pragma unroll
