@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       uint32_t cnt[18];
 #pragma unroll
       for (int c = 0; c < 18; ++c) cnt[c] = 0u;
-      unsigned long long st_cand = 0, st_table = 0, st_exact = 0, st_light = 0;
+      unsigned long long st_cand = 0, st_table = 0, st_exact = 0;
       const int64_t first = (int64_t)(bd + 1);
       const int64_t fw = first >> 5;
       // light nodes: cursors into their dense lists (fewer than 32 entries
@@ -553,6 +553,19 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         }
       }
       long long t_words1 = g.stats ? clock64() : 0;
+      if (g.stats) {
+        for (int d = 16; d; d >>= 1) {
+          st_cand += __shfl_xor_sync(0xffffffffu, st_cand, d);
+          st_table += __shfl_xor_sync(0xffffffffu, st_table, d);
+          st_exact += __shfl_xor_sync(0xffffffffu, st_exact, d);
+        }
+        if (lane == 0) {
+          atomicAdd(&g.stats[0], (unsigned long long)(W - fw));
+          atomicAdd(&g.stats[1], st_cand);
+          atomicAdd(&g.stats[2], st_table);
+          atomicAdd(&g.stats[3], st_exact);
+        }
+      }
       // flush the per-lane counters: lane c handles counter c
       uint32_t mine = 0u;
 #pragma unroll
@@ -829,6 +842,27 @@ __global__ void k_dense_fill(int64_t N, const int64_t* __restrict__ voff,
   }
 }
 
+// sort each node's dense list of fewer than 32 entries (the light nodes'
+// lists, read in ascending dense index by the dense-triangle kernel)
+__global__ void k_sort_short_lists(int64_t N, const int64_t* __restrict__ dvoff,
+                                   int32_t* __restrict__ dvedge) {
+  const int64_t v = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (v >= N) return;
+  const int64_t b = dvoff[v], e = dvoff[v + 1];
+  if (e - b > 32 || e - b < 2) return;
+  int32_t x = b + lane < e ? dvedge[b + lane] : 0x7fffffff;
+  for (int k = 2; k <= 32; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+      const bool up = (lane & k) == 0;
+      const bool lower = (lane & j) == 0;
+      x = (lower == up) ? min(x, y) : max(x, y);
+    }
+  }
+  if (b + lane < e) dvedge[b + lane] = x;
+}
+
 __global__ void k_size_bits(int64_t n_dense, int64_t W, const int32_t* __restrict__ drow,
                             const int64_t* __restrict__ eoff, int theta, uint32_t* __restrict__ sbits,
                             uint8_t* __restrict__ dsize) {
@@ -1021,6 +1055,8 @@ int prepare_split(mochy_ctx* ctx) {
     if (N > 0) {
       k_dense_fill<<<ceil_div(N, 8), 256, 0, st>>>(N, ctx->voff, ctx->vedge, ctx->dense_idx,
                                                    ctx->dvoff, ctx->dvedge);
+      MOCHY_LAUNCHED();
+      k_sort_short_lists<<<ceil_div(N, 8), 256, 0, st>>>(N, ctx->dvoff, ctx->dvedge);
       MOCHY_LAUNCHED();
     }
   }
