@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
 constexpr int kDThreads = 256;
 constexpr int kDWarps = kDThreads / 32;
 constexpr int kCeff = 16;          // effective sizes kept in the table
-constexpr int kCombo = 64;         // (xa, xb, xt), 2 bits each
+constexpr int kCombo = 64;         // (xa, xb, xt) with each count below 4
 
 struct WarpScratch {
   int64_t lpos[128];     // next unread entry of each light node's dense list
@@ -246,11 +246,24 @@ struct WarpScratch {
   uint32_t dirty[kCombo * kCeff / 32];
 };
 
-__device__ __forceinline__ void slice_add(uint32_t& c0, uint32_t& c1, uint32_t& ovf, uint32_t m) {
+// add one bit per lane to a 3-bit sliced counter (c0, c1, c2); a carry out
+// of the top bit marks the lane in ovf
+__device__ __forceinline__ void slice_add(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& ovf,
+                                          uint32_t m) {
   const uint32_t k0 = c0 & m;
   c0 ^= m;
-  ovf |= c1 & k0;
+  const uint32_t k1 = c1 & k0;
   c1 ^= k0;
+  ovf |= c2 & k1;
+  c2 ^= k1;
+}
+
+__device__ __forceinline__ uint32_t eq3(uint32_t c0, uint32_t c1, uint32_t c2, int v) {
+  return ((v & 1) ? c0 : ~c0) & ((v & 2) ? c1 : ~c1) & ((v & 4) ? c2 : ~c2);
+}
+
+__device__ __forceinline__ int sval3(uint32_t c0, uint32_t c1, uint32_t c2, int bit) {
+  return (int)((c0 >> bit) & 1u) + 2 * (int)((c1 >> bit) & 1u) + 4 * (int)((c2 >> bit) & 1u);
 }
 
 // lanes (bits) whose 2-bit sliced value equals v
@@ -280,6 +293,23 @@ __device__ __forceinline__ uint32_t ge4(uint32_t p0, uint32_t p1, uint32_t p2, u
 
 __device__ __forceinline__ int sval(uint32_t c0, uint32_t c1, int bit) {
   return (int)((c0 >> bit) & 1u) + 2 * (int)((c1 >> bit) & 1u);
+}
+
+// Per-warp table of (combination, effective size) counts for the rarer
+// combinations; counts of 4 or more in a group, or sizes beyond the table,
+// are added to the histogram directly.
+template <typename WS>
+__device__ __forceinline__ void table_add(WS& me, int combo3, int ce, uint32_t n,
+                                          unsigned long long* hist, const uint16_t* lut, int theta,
+                                          int A, int B, int x, int xa, int xb, int xt) {
+  if (xa < 4 && xb < 4 && xt < 4 && ce >= 1 && ce <= kCeff) {
+    const int key = ((xa * 4 + xb) * 4 + xt) * kCeff + ce - 1;
+    atomicAdd(&me.table[key], n);
+    atomicOr(&me.dirty[key >> 5], 1u << (key & 31));
+  } else {
+    add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, (long long)n);
+  }
+  (void)combo3;
 }
 
 // exact overlaps of e_k with e_a and e_b (and the part through heavy nodes)
@@ -442,10 +472,13 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         const int64_t w = inr ? w0 + lane : W - 1;
         uint32_t m = inr ? (A1[w] & __ldg(&B1[w])) : 0u;
         if (w == fw) m &= 0xffffffffu << (first & 31);
-        uint32_t a0 = 0, a1 = 0, b0 = 0, b1 = 0, t0 = 0, t1 = 0, ovf = 0;
-        for (int h = 0; h < nA; ++h) slice_add(a0, a1, ovf, __ldg(&g.nbits[(int64_t)me.hidx[0][h] * W + w]));
-        for (int h = 0; h < nB; ++h) slice_add(b0, b1, ovf, __ldg(&g.nbits[(int64_t)me.hidx[1][h] * W + w]));
-        for (int h = 0; h < nT; ++h) slice_add(t0, t1, ovf, __ldg(&g.nbits[(int64_t)me.hidx[2][h] * W + w]));
+        uint32_t a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0, t0 = 0, t1 = 0, t2 = 0, ovf = 0;
+        for (int h = 0; h < nA; ++h)
+          slice_add(a0, a1, a2, ovf, __ldg(&g.nbits[(int64_t)me.hidx[0][h] * W + w]));
+        for (int h = 0; h < nB; ++h)
+          slice_add(b0, b1, b2, ovf, __ldg(&g.nbits[(int64_t)me.hidx[1][h] * W + w]));
+        for (int h = 0; h < nT; ++h)
+          slice_add(t0, t1, t2, ovf, __ldg(&g.nbits[(int64_t)me.hidx[2][h] * W + w]));
         // light nodes with a dense index in this iteration's 32 words
         const int64_t hi64 = (w0 + 32) * 32;
         const int32_t hi = hi64 < 0x7fffffff ? (int32_t)hi64 : 0x7fffffff;
@@ -459,9 +492,9 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
             const int32_t kd = __shfl_sync(0xffffffffu, e, j);
             if ((int64_t)(kd >> 5) == w && inr) {
               const uint32_t bitm = 1u << (kd & 31);
-              if (grp == 0) slice_add(a0, a1, ovf, bitm);
-              else if (grp == 1) slice_add(b0, b1, ovf, bitm);
-              else slice_add(t0, t1, ovf, bitm);
+              if (grp == 0) slice_add(a0, a1, a2, ovf, bitm);
+              else if (grp == 1) slice_add(b0, b1, b2, ovf, bitm);
+              else slice_add(t0, t1, t2, ovf, bitm);
             }
           }
           const int32_t nx = __shfl_sync(0xffffffffu, e, nin & 31);
@@ -472,10 +505,10 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           }
           __syncwarp();
         }
-        const uint32_t za = a0 | a1, zb = b0 | b1, zt = t0 | t1;
+        const uint32_t za = a0 | a1 | a2, zb = b0 | b1 | b2, zt = t0 | t1 | t2;
         ovf &= m;
         const uint32_t valid = m & (za | zt) & (zb | zt) & ~ovf;
-        const uint32_t one_a = a0 & ~a1, one_b = b0 & ~b1, one_t = t0 & ~t1;
+        const uint32_t one_a = a0 & ~a1 & ~a2, one_b = b0 & ~b1 & ~b2, one_t = t0 & ~t1 & ~t2;
         const uint32_t s001 = valid & ~za & ~zb & one_t;
         const uint32_t s110 = valid & one_a & one_b & ~zt;
         uint32_t done = s001 | s110;
@@ -508,36 +541,42 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           st_table += __popc(valid & ~done);
           st_exact += __popc(ovf);
         }
-        // remaining candidates, one group of equal (xa, xb, xt, effective
-        // size) at a time: the group's mask is built bit-parallel
+        // remaining candidates, one overlap combination (xa, xb, xt) at a
+        // time: the combination's mask is built bit-parallel and split by
+        // effective size with the size planes
         uint32_t rest = valid & ~done;
         while (__any_sync(0xffffffffu, rest != 0u)) {
           if (!rest) continue;
           const int bit = __ffs(rest) - 1;
-          const int xa = sval(a0, a1, bit), xb = sval(b0, b1, bit), xt = sval(t0, t1, bit);
-          const uint32_t same = rest & eq2(a0, a1, xa) & eq2(b0, b1, xb) & eq2(t0, t1, xt);
-          const int C4 = (int)((p0 >> bit) & 1u) | ((int)((p1 >> bit) & 1u) << 1) |
-                         ((int)((p2 >> bit) & 1u) << 2) | ((int)((p3 >> bit) & 1u) << 3);
+          const int xa = sval3(a0, a1, a2, bit), xb = sval3(b0, b1, b2, bit),
+                    xt = sval3(t0, t1, t2, bit);
+          const uint32_t same = rest & eq3(a0, a1, a2, xa) & eq3(b0, b1, b2, xb) &
+                                eq3(t0, t1, t2, xt);
+          rest &= ~same;
           const int bound = xa + xb + 2 * xt + theta + 1;
-          uint32_t grp;
-          int ce;
-          if (C4 >= bound && bound <= 15) {
-            grp = same & ge4(p0, p1, p2, p3, bound);       // all sizes >= bound
-            ce = bound;
-          } else if (C4 < 15) {
-            grp = same & eq4(p0, p1, p2, p3, C4);          // this exact size
-            ce = C4;
-          } else {
-            grp = 1u << bit;                               // size >= 15: exact lookup
-            ce = min((int)g.dsize[w * 32 + bit], bound);
+          const int combo = (xa * 8 + xb) * 8 + xt;
+          const int cap = min(bound, 15);
+          // sizes below the cap one by one, the cap and above together
+          uint32_t left = same;
+          for (int c = 1; c < cap && left; ++c) {
+            const uint32_t grp = left & eq4(p0, p1, p2, p3, c);
+            if (!grp) continue;
+            left &= ~grp;
+            table_add(me, combo, c, (uint32_t)__popc(grp), hist, lut, theta, A, B, x, xa, xb, xt);
           }
-          rest &= ~grp;
-          if (ce <= kCeff) {
-            const int key = ((xa * 4 + xb) * 4 + xt) * kCeff + ce - 1;
-            atomicAdd(&me.table[key], (uint32_t)__popc(grp));
-            atomicOr(&me.dirty[key >> 5], 1u << (key & 31));
-          } else {
-            add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, __popc(grp));
+          if (left) {
+            if (bound <= 15) {
+              table_add(me, combo, bound, (uint32_t)__popc(left), hist, lut, theta, A, B, x, xa, xb,
+                        xt);
+            } else {
+              // sizes of 15 or more with a large bound: exact sizes
+              while (left) {
+                const int lb = __ffs(left) - 1;
+                left &= left - 1;
+                const int ce = min((int)g.dsize[w * 32 + lb], bound);
+                table_add(me, combo, ce, 1u, hist, lut, theta, A, B, x, xa, xb, xt);
+              }
+            }
           }
         }
         uint32_t e = ovf;
