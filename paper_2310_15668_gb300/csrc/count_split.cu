@@ -233,10 +233,13 @@ constexpr int kDWarps = kDThreads / 32;
 constexpr int kCeff = 16;          // effective sizes kept in the table
 constexpr int kCombo = 64;         // (xa, xb, xt) with each count below 4
 
+constexpr int kLight = 512;        // merged light-node entries per hyperwedge
+
 struct WarpScratch {
   int64_t lpos[128];     // next unread entry of each light node's dense list
   int64_t lend[128];     // end of that list
   int32_t lnext[128];    // dense index at lpos (INT_MAX when done)
+  int32_t lent[kLight];  // merged entries (dense index << 2 | group), ascending
   int32_t bnodes[64];
   int32_t hidx[3][64];   // heavy indices of groups A, B, T
   int32_t light[128];    // light nodes of e_a | e_b
@@ -449,8 +452,10 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       unsigned long long st_cand = 0, st_table = 0, st_exact = 0;
       const int64_t first = (int64_t)(bd + 1);
       const int64_t fw = first >> 5;
-      // light nodes: cursors into their dense lists (fewer than 32 entries
-      // each), skipping dense indices before `first`
+      // light nodes: their dense lists (fewer than 32 entries each) from
+      // `first` on, merged into one ascending list when they fit, else read
+      // through one cursor per node
+      int n_lent = 0;
       for (int l = 0; l < nL; ++l) {
         const int32_t v = me.light[l];
         const int64_t lb = g.dvoff[v], le = g.dvoff[v + 1];
@@ -462,8 +467,34 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           me.lend[l] = le;
           me.lnext[l] = lb + before < le ? nx : 0x7fffffff;
         }
+        const bool keep = e != 0x7fffffff && e >= first;
+        const unsigned kb = __ballot_sync(0xffffffffu, keep);
+        if (keep && n_lent + __popc(kb) <= kLight)
+          me.lent[n_lent + __popc(kb & ((1u << lane) - 1u))] = (e << 2) | me.lgrp[l];
+        n_lent += __popc(kb);
+      }
+      const bool merged = n_lent <= kLight;
+      if (merged && n_lent > 1) {
+        // bitonic sort of the merged entries (padded to a power of two)
+        int np = 2;
+        while (np < n_lent) np <<= 1;
+        for (int q = n_lent + lane; q < np; q += 32) me.lent[q] = 0x7fffffff;
+        __syncwarp();
+        for (int k = 2; k <= np; k <<= 1)
+          for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < np; i += 32) {
+              const int ixj = i ^ j;
+              if (ixj > i) {
+                const int32_t u = me.lent[i], v2 = me.lent[ixj];
+                const bool up = (i & k) == 0;
+                if ((u > v2) == up) { me.lent[i] = v2; me.lent[ixj] = u; }
+              }
+            }
+            __syncwarp();
+          }
       }
       __syncwarp();
+      int lcur = 0;   // next merged entry
       long long t_words0 = g.stats ? clock64() : 0;
       // uniform loop: every lane runs every iteration (lanes past the end see
       // an empty word), so the warp stays converged
@@ -482,28 +513,48 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         // light nodes with a dense index in this iteration's 32 words
         const int64_t hi64 = (w0 + 32) * 32;
         const int32_t hi = hi64 < 0x7fffffff ? (int32_t)hi64 : 0x7fffffff;
-        for (int l = 0; l < nL; ++l) {
-          if (me.lnext[l] >= hi) continue;              // uniform: same value on all lanes
-          const int64_t pos = me.lpos[l], le = me.lend[l];
-          const int32_t e = pos + lane < le ? g.dvedge[pos + lane] : 0x7fffffff;
-          const int nin = __popc(__ballot_sync(0xffffffffu, e < hi));
-          const int grp = me.lgrp[l];
-          for (int j = 0; j < nin; ++j) {
-            const int32_t kd = __shfl_sync(0xffffffffu, e, j);
-            if ((int64_t)(kd >> 5) == w && inr) {
-              const uint32_t bitm = 1u << (kd & 31);
-              if (grp == 0) slice_add(a0, a1, a2, ovf, bitm);
-              else if (grp == 1) slice_add(b0, b1, b2, ovf, bitm);
-              else slice_add(t0, t1, t2, ovf, bitm);
+        if (merged) {
+          while (lcur < n_lent) {
+            const int32_t e = lcur + lane < n_lent ? me.lent[lcur + lane] : 0x7fffffff;
+            const int nin = __popc(__ballot_sync(0xffffffffu, (e >> 2) < hi && e != 0x7fffffff));
+            for (int j = 0; j < nin; ++j) {
+              const int32_t ej = __shfl_sync(0xffffffffu, e, j);
+              const int32_t kd = ej >> 2;
+              if ((int64_t)(kd >> 5) == w && inr) {
+                const uint32_t bitm = 1u << (kd & 31);
+                const int grp = ej & 3;
+                if (grp == 0) slice_add(a0, a1, a2, ovf, bitm);
+                else if (grp == 1) slice_add(b0, b1, b2, ovf, bitm);
+                else slice_add(t0, t1, t2, ovf, bitm);
+              }
             }
+            lcur += nin;
+            if (nin < 32) break;
           }
-          const int32_t nx = __shfl_sync(0xffffffffu, e, nin & 31);
-          __syncwarp();
-          if (lane == 0) {
-            me.lpos[l] = pos + nin;
-            me.lnext[l] = pos + nin < le ? nx : 0x7fffffff;
+        } else {
+          for (int l = 0; l < nL; ++l) {
+            if (me.lnext[l] >= hi) continue;              // uniform: same value on all lanes
+            const int64_t pos = me.lpos[l], le = me.lend[l];
+            const int32_t e = pos + lane < le ? g.dvedge[pos + lane] : 0x7fffffff;
+            const int nin = __popc(__ballot_sync(0xffffffffu, e < hi));
+            const int grp = me.lgrp[l];
+            for (int j = 0; j < nin; ++j) {
+              const int32_t kd = __shfl_sync(0xffffffffu, e, j);
+              if ((int64_t)(kd >> 5) == w && inr) {
+                const uint32_t bitm = 1u << (kd & 31);
+                if (grp == 0) slice_add(a0, a1, a2, ovf, bitm);
+                else if (grp == 1) slice_add(b0, b1, b2, ovf, bitm);
+                else slice_add(t0, t1, t2, ovf, bitm);
+              }
+            }
+            const int32_t nx = __shfl_sync(0xffffffffu, e, nin & 31);
+            __syncwarp();
+            if (lane == 0) {
+              me.lpos[l] = pos + nin;
+              me.lnext[l] = pos + nin < le ? nx : 0x7fffffff;
+            }
+            __syncwarp();
           }
-          __syncwarp();
         }
         const uint32_t za = a0 | a1 | a2, zb = b0 | b1 | b2, zt = t0 | t1 | t2;
         ovf &= m;
@@ -541,41 +592,63 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           st_table += __popc(valid & ~done);
           st_exact += __popc(ovf);
         }
-        // remaining candidates, one overlap combination (xa, xb, xt) at a
-        // time: the combination's mask is built bit-parallel and split by
-        // effective size with the size planes
-        uint32_t rest = valid & ~done;
-        while (__any_sync(0xffffffffu, rest != 0u)) {
-          if (!rest) continue;
-          const int bit = __ffs(rest) - 1;
-          const int xa = sval3(a0, a1, a2, bit), xb = sval3(b0, b1, b2, bit),
-                    xt = sval3(t0, t1, t2, bit);
-          const uint32_t same = rest & eq3(a0, a1, a2, xa) & eq3(b0, b1, b2, xb) &
-                                eq3(t0, t1, t2, xt);
-          rest &= ~same;
-          const int bound = xa + xb + 2 * xt + theta + 1;
-          const int combo = (xa * 8 + xb) * 8 + xt;
-          const int cap = min(bound, 15);
-          // sizes below the cap one by one, the cap and above together
-          uint32_t left = same;
-          for (int c = 1; c < cap && left; ++c) {
-            const uint32_t grp = left & eq4(p0, p1, p2, p3, c);
-            if (!grp) continue;
-            left &= ~grp;
-            table_add(me, combo, c, (uint32_t)__popc(grp), hist, lut, theta, A, B, x, xa, xb, xt);
+        // remaining candidates, processed by the whole warp 32 at a time:
+        // lane i takes the i-th remaining candidate of the iteration (from any
+        // lane's word), reads that word's counters by shuffle, and equal
+        // (combination, size) keys are added once per group of lanes
+        {
+          const uint32_t rest = valid & ~done;
+          const int rc = __popc(rest);
+          int incl = rc;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
           }
-          if (left) {
-            if (bound <= 15) {
-              table_add(me, combo, bound, (uint32_t)__popc(left), hist, lut, theta, A, B, x, xa, xb,
-                        xt);
-            } else {
-              // sizes of 15 or more with a large bound: exact sizes
-              while (left) {
-                const int lb = __ffs(left) - 1;
-                left &= left - 1;
-                const int ce = min((int)g.dsize[w * 32 + lb], bound);
-                table_add(me, combo, ce, 1u, hist, lut, theta, A, B, x, xa, xb, xt);
-              }
+          const int total = __shfl_sync(0xffffffffu, incl, 31);
+          for (int base = 0; base < total; base += 32) {
+            const int item = base + lane;
+            // source lane: the first lane whose inclusive count exceeds item
+            int src = 0;
+#pragma unroll
+            for (int st = 16; st; st >>= 1) {
+              const int probe = __shfl_sync(0xffffffffu, incl, src + st - 1);
+              if (probe <= item) src += st;
+            }
+            src &= 31;
+            const int ex = __shfl_sync(0xffffffffu, incl - rc, src);
+            const uint32_t rs = __shfl_sync(0xffffffffu, rest, src);
+            const uint32_t sa0 = __shfl_sync(0xffffffffu, a0, src), sa1 = __shfl_sync(0xffffffffu, a1, src),
+                           sa2 = __shfl_sync(0xffffffffu, a2, src);
+            const uint32_t sb0 = __shfl_sync(0xffffffffu, b0, src), sb1 = __shfl_sync(0xffffffffu, b1, src),
+                           sb2 = __shfl_sync(0xffffffffu, b2, src);
+            const uint32_t st0 = __shfl_sync(0xffffffffu, t0, src), st1 = __shfl_sync(0xffffffffu, t1, src),
+                           st2 = __shfl_sync(0xffffffffu, t2, src);
+            const uint32_t sp0 = __shfl_sync(0xffffffffu, p0, src), sp1 = __shfl_sync(0xffffffffu, p1, src),
+                           sp2 = __shfl_sync(0xffffffffu, p2, src), sp3 = __shfl_sync(0xffffffffu, p3, src);
+            const int64_t sw = __shfl_sync(0xffffffffu, w, src);
+            const bool act = item < total;
+            int key = -1;
+            int xa = 0, xb = 0, xt = 0, ce = 0;
+            if (act) {
+              const int bit = __fns(rs, 0, item - ex + 1);
+              xa = sval3(sa0, sa1, sa2, bit);
+              xb = sval3(sb0, sb1, sb2, bit);
+              xt = sval3(st0, st1, st2, bit);
+              int C = (int)((sp0 >> bit) & 1u) | ((int)((sp1 >> bit) & 1u) << 1) |
+                      ((int)((sp2 >> bit) & 1u) << 2) | ((int)((sp3 >> bit) & 1u) << 3);
+              if (C >= 15) C = g.dsize[sw * 32 + bit];
+              ce = min(C, xa + xb + 2 * xt + theta + 1);
+              if (xa < 4 && xb < 4 && xt < 4 && ce <= kCeff)
+                key = ((xa * 4 + xb) * 4 + xt) * kCeff + ce - 1;
+            }
+            if (act && key < 0) {
+              add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, 1);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0) {
+              atomicAdd(&me.table[key], (uint32_t)__popc(peers));
+              atomicOr(&me.dirty[key >> 5], 1u << (key & 31));
             }
           }
         }
