@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
 // ---------------------------------------------------------------------------
 constexpr int kDThreads = 256;
 constexpr int kDWarps = kDThreads / 32;
+constexpr int kHoist = 6;          // heavy bitmaps whose pointers stay in registers
 constexpr int kCeff = 16;          // effective sizes kept in the table
 constexpr int kCombo = 64;         // (xa, xb, xt) with each count below 4
 
@@ -443,6 +444,16 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         __syncwarp();
       }
       const int nA = me.n[0], nB = me.n[1], nT = me.n[2], nL = me.n[3];
+      const int nH = nA + nB + nT;
+      const uint32_t* hp[kHoist];
+      uint32_t hgrp = 0u;
+#pragma unroll
+      for (int h = 0; h < kHoist; ++h) {
+        const int gr = h < nA ? 0 : h < nA + nB ? 1 : 2;
+        const int q = gr == 0 ? h : gr == 1 ? h - nA : h - nA - nB;
+        hp[h] = h < nH ? g.nbits + (int64_t)me.hidx[gr][q] * W : g.nbits;
+        hgrp |= (uint32_t)gr << (2 * h);
+      }
       const uint32_t* B1 = g.dbits + (int64_t)bd * 2 * W;
       // per-lane counters: q001[4], q011[5], q101[5], q110[4] (theta = 1) or
       // q001[5], q110[5] by size class (other theta)
@@ -504,12 +515,32 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         uint32_t m = inr ? (A1[w] & __ldg(&B1[w])) : 0u;
         if (w == fw) m &= 0xffffffffu << (first & 31);
         uint32_t a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0, t0 = 0, t1 = 0, t2 = 0, ovf = 0;
-        for (int h = 0; h < nA; ++h)
-          slice_add(a0, a1, a2, ovf, __ldg(&g.nbits[(int64_t)me.hidx[0][h] * W + w]));
-        for (int h = 0; h < nB; ++h)
-          slice_add(b0, b1, b2, ovf, __ldg(&g.nbits[(int64_t)me.hidx[1][h] * W + w]));
-        for (int h = 0; h < nT; ++h)
-          slice_add(t0, t1, t2, ovf, __ldg(&g.nbits[(int64_t)me.hidx[2][h] * W + w]));
+        {
+          // the first kHoist heavy bitmaps: pointers in registers, loads
+          // issued together; any further ones from the shared lists
+          uint32_t hv[kHoist];
+#pragma unroll
+          for (int h = 0; h < kHoist; ++h) hv[h] = h < nH ? __ldg(hp[h] + w) : 0u;
+#pragma unroll
+          for (int h = 0; h < kHoist; ++h) {
+            if (h >= nH) break;
+            const int gr = (hgrp >> (2 * h)) & 3;
+            if (gr == 0) slice_add(a0, a1, a2, ovf, hv[h]);
+            else if (gr == 1) slice_add(b0, b1, b2, ovf, hv[h]);
+            else slice_add(t0, t1, t2, ovf, hv[h]);
+          }
+          if (nH > kHoist) {
+            int h = 0;
+            for (int gg = 0; gg < 3; ++gg)
+              for (int q = 0; q < me.n[gg]; ++q, ++h) {
+                if (h < kHoist) continue;
+                const uint32_t v = __ldg(&g.nbits[(int64_t)me.hidx[gg][q] * W + w]);
+                if (gg == 0) slice_add(a0, a1, a2, ovf, v);
+                else if (gg == 1) slice_add(b0, b1, b2, ovf, v);
+                else slice_add(t0, t1, t2, ovf, v);
+              }
+          }
+        }
         // light nodes with a dense index in this iteration's 32 words
         const int64_t hi64 = (w0 + 32) * 32;
         const int32_t hi = hi64 < 0x7fffffff ? (int32_t)hi64 : 0x7fffffff;
@@ -649,6 +680,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
             if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0) {
               atomicAdd(&me.table[key], (uint32_t)__popc(peers));
               atomicOr(&me.dirty[key >> 5], 1u << (key & 31));
+              if (g.stats) atomicAdd(&g.stats[8 + key / kCeff], (unsigned long long)__popc(peers));
             }
           }
         }
@@ -1222,6 +1254,14 @@ struct PhaseTimer {
     }
     if (c->stats)
       cudaMemcpy(c->last_stats, c->stats, sizeof(c->last_stats), cudaMemcpyDeviceToHost);
+    if (c->stats && print) {
+      unsigned long long combo[64];
+      cudaMemcpy(combo, c->stats + 8, sizeof(combo), cudaMemcpyDeviceToHost);
+      fprintf(stderr, "[mochy]   rest combinations (xa,xb,xt): ");
+      for (int q = 0; q < 64; ++q)
+        if (combo[q]) fprintf(stderr, "(%d,%d,%d)=%llu ", q >> 4, (q >> 2) & 3, q & 3, combo[q]);
+      fprintf(stderr, "\n");
+    }
     if (print) {
       fprintf(stderr, "[mochy] split exact: E=%lld dense=%lld (threshold %d, %lld words) heavy=%lld\n",
               (long long)c->n_edges, (long long)c->n_dense, c->dense_thr_used,
@@ -1244,10 +1284,10 @@ int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
   PhaseTimer timer(ctx);
   if (timer.on && !ctx->stats) {
     void* p;
-    MOCHY_TRY(dev_alloc(ctx, &p, 8 * sizeof(unsigned long long)));
+    MOCHY_TRY(dev_alloc(ctx, &p, 72 * sizeof(unsigned long long)));
     ctx->stats = (unsigned long long*)p;
   }
-  if (ctx->stats) MOCHY_CUDA(cudaMemsetAsync(ctx->stats, 0, 8 * sizeof(unsigned long long), st));
+  if (ctx->stats) MOCHY_CUDA(cudaMemsetAsync(ctx->stats, 0, 72 * sizeof(unsigned long long), st));
   timer.mark("start");
   MOCHY_TRY(prepare_split(ctx));
   timer.mark("prepare");
