@@ -230,7 +230,6 @@ __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
 // ---------------------------------------------------------------------------
 constexpr int kDThreads = 256;
 constexpr int kDWarps = kDThreads / 32;
-constexpr int kHoist = 6;          // heavy bitmaps whose pointers stay in registers
 constexpr int kCeff = 16;          // effective sizes kept in the table
 constexpr int kCombo = 64;         // (xa, xb, xt) with each count below 4
 
@@ -342,17 +341,27 @@ __device__ __forceinline__ Overlap overlaps(const int32_t* anodes, int A, const 
 // 4, 5, 5 and 4); with another theta only (0,0,1) and (1,1,0) are, per size
 // class.  Bit-planes p0..p3 hold min(|e_k|, 15) of the candidates.
 struct SizeMasks {
-  uint32_t e1, e2, e3, e4, ge4, ge5;
+  uint32_t e1, e2, e3, e4, e5, ge4, ge5, ge6;
   __device__ __forceinline__ SizeMasks(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3) {
     const uint32_t lo = ~p3 & ~p2;
     e1 = lo & ~p1 & p0;
     e2 = lo & p1 & ~p0;
     e3 = lo & p1 & p0;
     e4 = ~p3 & p2 & ~p1 & ~p0;
+    e5 = ~p3 & p2 & ~p1 & p0;
     ge4 = p3 | p2;
     ge5 = ge4 & ~e4;
+    ge6 = ge5 & ~e5;
   }
 };
+
+// Popcounted combinations for theta = 1: (xa, xb, xt), smallest possible
+// effective size, number of size bins (the last bin holds every size from
+// the bound xa + xb + 2 xt + 2 up, where the codes stop changing).
+__constant__ int c_pop[7][5] = {
+    {0, 0, 1, 1, 4}, {0, 1, 1, 2, 4}, {1, 0, 1, 2, 4}, {1, 1, 0, 2, 3},
+    {0, 2, 1, 3, 4}, {1, 1, 1, 3, 4}, {0, 0, 2, 2, 5}};
+constexpr int kPopBins = 28;   // total bins, counted two per register
 
 template <bool kTheta1>
 __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
@@ -444,22 +453,11 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         __syncwarp();
       }
       const int nA = me.n[0], nB = me.n[1], nT = me.n[2], nL = me.n[3];
-      const int nH = nA + nB + nT;
-      const uint32_t* hp[kHoist];
-      uint32_t hgrp = 0u;
-#pragma unroll
-      for (int h = 0; h < kHoist; ++h) {
-        const int gr = h < nA ? 0 : h < nA + nB ? 1 : 2;
-        const int q = gr == 0 ? h : gr == 1 ? h - nA : h - nA - nB;
-        hp[h] = h < nH ? g.nbits + (int64_t)me.hidx[gr][q] * W : g.nbits;
-        hgrp |= (uint32_t)gr << (2 * h);
-      }
       const uint32_t* B1 = g.dbits + (int64_t)bd * 2 * W;
-      // per-lane counters: q001[4], q011[5], q101[5], q110[4] (theta = 1) or
-      // q001[5], q110[5] by size class (other theta)
-      uint32_t cnt[18];
+      // per-lane counters: 14 pairs of 16-bit bins (theta = 1) or 10 bins
+      uint32_t cnt[14];
 #pragma unroll
-      for (int c = 0; c < 18; ++c) cnt[c] = 0u;
+      for (int c = 0; c < 14; ++c) cnt[c] = 0u;
       unsigned long long st_cand = 0, st_table = 0, st_exact = 0;
       const int64_t first = (int64_t)(bd + 1);
       const int64_t fw = first >> 5;
@@ -515,32 +513,12 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         uint32_t m = inr ? (A1[w] & __ldg(&B1[w])) : 0u;
         if (w == fw) m &= 0xffffffffu << (first & 31);
         uint32_t a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0, t0 = 0, t1 = 0, t2 = 0, ovf = 0;
-        {
-          // the first kHoist heavy bitmaps: pointers in registers, loads
-          // issued together; any further ones from the shared lists
-          uint32_t hv[kHoist];
-#pragma unroll
-          for (int h = 0; h < kHoist; ++h) hv[h] = h < nH ? __ldg(hp[h] + w) : 0u;
-#pragma unroll
-          for (int h = 0; h < kHoist; ++h) {
-            if (h >= nH) break;
-            const int gr = (hgrp >> (2 * h)) & 3;
-            if (gr == 0) slice_add(a0, a1, a2, ovf, hv[h]);
-            else if (gr == 1) slice_add(b0, b1, b2, ovf, hv[h]);
-            else slice_add(t0, t1, t2, ovf, hv[h]);
-          }
-          if (nH > kHoist) {
-            int h = 0;
-            for (int gg = 0; gg < 3; ++gg)
-              for (int q = 0; q < me.n[gg]; ++q, ++h) {
-                if (h < kHoist) continue;
-                const uint32_t v = __ldg(&g.nbits[(int64_t)me.hidx[gg][q] * W + w]);
-                if (gg == 0) slice_add(a0, a1, a2, ovf, v);
-                else if (gg == 1) slice_add(b0, b1, b2, ovf, v);
-                else slice_add(t0, t1, t2, ovf, v);
-              }
-          }
-        }
+        for (int h = 0; h < nA; ++h)
+          slice_add(a0, a1, a2, ovf, __ldg(&g.nbits[(int64_t)me.hidx[0][h] * W + w]));
+        for (int h = 0; h < nB; ++h)
+          slice_add(b0, b1, b2, ovf, __ldg(&g.nbits[(int64_t)me.hidx[1][h] * W + w]));
+        for (int h = 0; h < nT; ++h)
+          slice_add(t0, t1, t2, ovf, __ldg(&g.nbits[(int64_t)me.hidx[2][h] * W + w]));
         // light nodes with a dense index in this iteration's 32 words
         const int64_t hi64 = (w0 + 32) * 32;
         const int32_t hi = hi64 < 0x7fffffff ? (int32_t)hi64 : 0x7fffffff;
@@ -597,19 +575,29 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         const uint32_t p0 = __ldg(&P0[w]), p1 = __ldg(&P1[w]), p2 = __ldg(&P2[w]), p3 = __ldg(&P3[w]);
         const SizeMasks sz(p0, p1, p2, p3);
         if (kTheta1) {
+          const uint32_t two_b = ~b0 & b1 & ~b2, two_t = ~t0 & t1 & ~t2;
           const uint32_t s011 = valid & ~za & one_b & one_t;
           const uint32_t s101 = valid & one_a & ~zb & one_t;
-          done |= s011 | s101;
-          cnt[0] += __popc(s001 & sz.e1); cnt[1] += __popc(s001 & sz.e2);
-          cnt[2] += __popc(s001 & sz.e3); cnt[3] += __popc(s001 & sz.ge4);
-          cnt[4] += __popc(s011 & sz.e1); cnt[5] += __popc(s011 & sz.e2);
-          cnt[6] += __popc(s011 & sz.e3); cnt[7] += __popc(s011 & sz.e4);
-          cnt[8] += __popc(s011 & sz.ge5);
-          cnt[9] += __popc(s101 & sz.e1); cnt[10] += __popc(s101 & sz.e2);
-          cnt[11] += __popc(s101 & sz.e3); cnt[12] += __popc(s101 & sz.e4);
-          cnt[13] += __popc(s101 & sz.ge5);
-          cnt[14] += __popc(s110 & sz.e1); cnt[15] += __popc(s110 & sz.e2);
-          cnt[16] += __popc(s110 & sz.e3); cnt[17] += __popc(s110 & sz.ge4);
+          const uint32_t s021 = valid & ~za & two_b & one_t;
+          const uint32_t s111 = valid & one_a & one_b & one_t;
+          const uint32_t s002 = valid & ~za & ~zb & two_t;
+          done |= s011 | s101 | s021 | s111 | s002;
+          // bins: (0,0,1) 1,2,3,4+ | (0,1,1) 2,3,4,5+ | (1,0,1) 2,3,4,5+ |
+          // (1,1,0) 2,3,4+ | (0,2,1) 3,4,5,6+ | (1,1,1) 3,4,5,6+ | (0,0,2) 2,3,4,5,6+
+          cnt[0] += __popc(s001 & sz.e1) | (__popc(s001 & sz.e2) << 16);
+          cnt[1] += __popc(s001 & sz.e3) | (__popc(s001 & sz.ge4) << 16);
+          cnt[2] += __popc(s011 & sz.e2) | (__popc(s011 & sz.e3) << 16);
+          cnt[3] += __popc(s011 & sz.e4) | (__popc(s011 & sz.ge5) << 16);
+          cnt[4] += __popc(s101 & sz.e2) | (__popc(s101 & sz.e3) << 16);
+          cnt[5] += __popc(s101 & sz.e4) | (__popc(s101 & sz.ge5) << 16);
+          cnt[6] += __popc(s110 & sz.e2) | (__popc(s110 & sz.e3) << 16);
+          cnt[7] += __popc(s110 & sz.ge4) | (__popc(s021 & sz.e3) << 16);
+          cnt[8] += __popc(s021 & sz.e4) | (__popc(s021 & sz.e5) << 16);
+          cnt[9] += __popc(s021 & sz.ge6) | (__popc(s111 & sz.e3) << 16);
+          cnt[10] += __popc(s111 & sz.e4) | (__popc(s111 & sz.e5) << 16);
+          cnt[11] += __popc(s111 & sz.ge6) | (__popc(s002 & sz.e2) << 16);
+          cnt[12] += __popc(s002 & sz.e3) | (__popc(s002 & sz.e4) << 16);
+          cnt[13] += __popc(s002 & sz.e5) | (__popc(s002 & sz.ge6) << 16);
         } else {
 #pragma unroll
           for (int c = 0; c < kClasses; ++c) {
@@ -710,23 +698,31 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           atomicAdd(&g.stats[3], st_exact);
         }
       }
-      // flush the per-lane counters: lane c handles counter c
+      // flush the per-lane counters: lane c handles counter c (theta = 1:
+      // counters are pairs of 16-bit bins)
       uint32_t mine = 0u;
+      if (kTheta1) {
 #pragma unroll
-      for (int c = 0; c < 18; ++c) {
-        const uint32_t v = __reduce_add_sync(0xffffffffu, cnt[c]);
-        if (lane == c) mine = v;
-      }
-      if (mine) {
-        if (kTheta1) {
-          // counters 0-3: (0,0,1) sizes 1..4+; 4-8: (0,1,1) 1..5+; 9-13: (1,0,1)
-          // 1..5+; 14-17: (1,1,0) 1..4+
-          const int s = lane < 4 ? 0 : lane < 9 ? 1 : lane < 14 ? 2 : 3;
-          const int c = lane - (s == 0 ? 0 : s == 1 ? 4 : s == 2 ? 9 : 14);
-          const int xa = s == 2 || s == 3 ? 1 : 0, xb = s == 1 || s == 3 ? 1 : 0,
-                    xt = s == 3 ? 0 : 1;
-          add_triangle(hist, lut, theta, A, B, c + 1, x, xb + xt, xa + xt, xt, (long long)mine);
-        } else if (lane < 2 * kClasses) {
+        for (int c = 0; c < 14; ++c) {
+          const uint32_t lo = __reduce_add_sync(0xffffffffu, cnt[c] & 0xffffu);
+          const uint32_t hi2 = __reduce_add_sync(0xffffffffu, cnt[c] >> 16);
+          if (lane == 2 * c) mine = lo;
+          if (lane == 2 * c + 1) mine = hi2;
+        }
+        if (mine && lane < kPopBins) {
+          int s2 = 0, base = 0;
+          while (base + c_pop[s2][4] <= lane) { base += c_pop[s2][4]; ++s2; }
+          const int xa = c_pop[s2][0], xb = c_pop[s2][1], xt = c_pop[s2][2];
+          const int ce = c_pop[s2][3] + (lane - base);
+          add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, (long long)mine);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 2 * kClasses; ++c) {
+          const uint32_t v = __reduce_add_sync(0xffffffffu, cnt[c]);
+          if (lane == c) mine = v;
+        }
+        if (mine && lane < 2 * kClasses) {
           const int C = class_rep(lane % kClasses, theta);
           add_triangle(hist, lut, theta, A, B, C, x, 1, 1, lane < kClasses ? 1 : 0, (long long)mine);
         }
@@ -1262,6 +1258,7 @@ struct PhaseTimer {
         if (combo[q]) fprintf(stderr, "(%d,%d,%d)=%llu ", q >> 4, (q >> 2) & 3, q & 3, combo[q]);
       fprintf(stderr, "\n");
     }
+
     if (print) {
       fprintf(stderr, "[mochy] split exact: E=%lld dense=%lld (threshold %d, %lld words) heavy=%lld\n",
               (long long)c->n_edges, (long long)c->n_dense, c->dense_thr_used,
