@@ -11,9 +11,12 @@
 //                 rows, f_d = S_d / S the chance that a neighbour is dense
 //                 and W = n_dense / 32 words;
 //   sparse part ~ sum over sparse rows of deg^2 (pairs of neighbours probed).
-// The dense term overestimates the words scanned about twofold (dense rows
-// are ordered by degree), and a scanned word and a probed pair cost about
-// the same on GB300, so the word term gets weight 0.5.
+// Measured on GB300 (medium workload, thresholds 512..8192): the words the
+// dense kernel scans hardly fall as the threshold rises, because dense rows
+// are ordered by degree and most words come from the highest-degree rows,
+// while the model's dense term falls steeply; a scanned word costs about as
+// much as a probed pair.  A weight of 0.1 on the model's dense term puts the
+// minimum where the measured total is smallest.
 #include <cmath>
 #include <vector>
 
@@ -36,7 +39,7 @@ int choose_dense_threshold(mochy_ctx* ctx) {
     deg[i] = off[i + 1] - off[i];
     S += (double)deg[i];
   }
-  const double word_weight = 0.5;
+  const double word_weight = 0.1;
   int best = -1;
   double best_cost = 0.0;
   for (int64_t thr = 32; thr <= (int64_t)1 << 20; thr <<= 1) {
