@@ -213,7 +213,7 @@ def run_gpu(args):
 
     for _ in range(args.warmup):
         step()
-    B.mochy_trace(ctx.h, True)
+    B.mochy_trace(ctx.h, 1)            # phase events only: no effect on the kernels
     phases = []
     launches0 = B.mochy_kernel_launches()
     if ws > 1:
@@ -231,7 +231,7 @@ def run_gpu(args):
         torch.distributed.barrier()
     launches = B.mochy_kernel_launches() - launches0
     ms = start.elapsed_time(end)
-    B.mochy_trace(ctx.h, False)
+    B.mochy_trace(ctx.h, 0)
     t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
     total = torch.tensor([float(instances) * args.steps], dtype=torch.float64, device="cuda")
     if ws > 1:
@@ -239,6 +239,12 @@ def run_gpu(args):
         torch.distributed.all_reduce(total)
     ms_max = float(t_max.item())
     value = float(total.item()) / (ms_max / 1000.0)
+
+    # kernel statistics (scanned words) from one more, untimed step at trace level 2
+    B.mochy_trace(ctx.h, 2)
+    step()
+    stats_trace = B.mochy_trace_read(ctx.h)
+    B.mochy_trace(ctx.h, 0)
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -265,7 +271,7 @@ def run_gpu(args):
     keys = set().union(*(p["phases_ms"].keys() for p in phases)) if phases else set()
     avg = {k: float(np.mean([p["phases_ms"].get(k, 0.0) for p in phases])) for k in keys}
     dom = max(avg, key=avg.get) if avg else None
-    st = phases[-1] if phases else {}
+    st = stats_trace
     roof = None
     if dom == "dense triangles" and avg[dom] > 0:
         # algorithmic bytes: every scanned word reads one word of the partner

@@ -174,12 +174,14 @@ int mochy_motif_pattern(int kind, int32_t id, uint8_t regions_out[7]);
 /* cudaStream_t the context runs on (as void*), for event timing. */
 void* mochy_stream(mochy_ctx* ctx);
 
-/* Tracing: with enable != 0 the exact count records the duration of each of
- * its phases (CUDA events on the context's stream) and kernel statistics;
- * mochy_trace_read writes them for the last traced call as one JSON object
- * into buf (len bytes).  The environment variable MOCHY_TRACE=1 turns tracing
- * on for every context and also prints the phases to stderr. */
-int mochy_trace(mochy_ctx* ctx, int enable);
+/* Tracing of the exact count: level 1 records the duration of each of its
+ * phases (CUDA events on the context's stream, no effect on the kernels);
+ * level 2 also counts kernel statistics (scanned words, candidates, cycles
+ * per section), which slows the kernels; 0 turns tracing off.
+ * mochy_trace_read writes the last traced call as one JSON object into buf
+ * (len bytes).  The environment variable MOCHY_TRACE=1 selects level 2 for
+ * every context and also prints to stderr. */
+int mochy_trace(mochy_ctx* ctx, int level);
 int mochy_trace_read(mochy_ctx* ctx, char* buf, int64_t len);
 
 /* Bytes of device memory the context holds now. */

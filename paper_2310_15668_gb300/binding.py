@@ -223,8 +223,8 @@ def mochy_device_bytes(ctx: int) -> int:
     return int(load_library().mochy_device_bytes(ctx))
 
 
-def mochy_trace(ctx: int, enable: bool) -> None:
-    _check(load_library().mochy_trace(ctx, 1 if enable else 0), "mochy_trace")
+def mochy_trace(ctx: int, level: int) -> None:
+    _check(load_library().mochy_trace(ctx, int(level)), "mochy_trace")
 
 
 def mochy_trace_read(ctx: int) -> dict:

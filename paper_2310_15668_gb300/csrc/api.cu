@@ -490,7 +490,7 @@ void* mochy_stream(mochy_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; 
 
 int mochy_trace(mochy_ctx* ctx, int enable) {
   if (!ctx) return fail(MOCHY_E_INVALID, "null context");
-  ctx->trace = enable != 0;
+  ctx->trace = enable < 0 ? 0 : (enable > 2 ? 2 : enable);
   return MOCHY_OK;
 }
 

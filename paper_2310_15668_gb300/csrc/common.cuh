@@ -131,7 +131,7 @@ struct mochy_ctx {
 
   // tracing: per-phase durations of the last traced call (CUDA events on the
   // context's stream) and kernel statistics
-  bool trace = false;
+  int trace = 0;                       // 0 off, 1 phase events, 2 + kernel statistics
   int n_phases = 0;
   char phase_name[8][24];
   double phase_ms[8];

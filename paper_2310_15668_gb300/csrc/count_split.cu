@@ -1227,10 +1227,12 @@ struct PhaseTimer {
   cudaEvent_t ev[8];
   const char* name[8];
   int n = 0;
+  bool stats = false;
   PhaseTimer(const mochy_ctx* c) : st(c->stream) {
     const char* e = getenv("MOCHY_TRACE");
     print = e && e[0] && e[0] != '0';
-    on = c->trace || print;
+    on = c->trace > 0 || print;
+    stats = c->trace > 1 || print;
   }
   void mark(const char* what) {
     if (!on || n >= 8) return;
@@ -1240,6 +1242,7 @@ struct PhaseTimer {
   }
   void report(mochy_ctx* c) {
     if (!on || n < 2) return;
+    if (!stats) memset(c->last_stats, 0, sizeof(c->last_stats));
     cudaEventSynchronize(ev[n - 1]);
     c->n_phases = 0;
     for (int i = 1; i < n; ++i) {
@@ -1248,9 +1251,9 @@ struct PhaseTimer {
       snprintf(c->phase_name[c->n_phases], sizeof(c->phase_name[0]), "%s", name[i]);
       c->phase_ms[c->n_phases++] = ms;
     }
-    if (c->stats)
+    if (stats)
       cudaMemcpy(c->last_stats, c->stats, sizeof(c->last_stats), cudaMemcpyDeviceToHost);
-    if (c->stats && print) {
+    if (stats && print) {
       unsigned long long combo[64];
       cudaMemcpy(combo, c->stats + 8, sizeof(combo), cudaMemcpyDeviceToHost);
       fprintf(stderr, "[mochy]   rest combinations (xa,xb,xt): ");
@@ -1265,7 +1268,7 @@ struct PhaseTimer {
               (long long)c->wwords, (long long)c->n_heavy);
       for (int i = 0; i < c->n_phases; ++i)
         fprintf(stderr, "[mochy]   %-18s %10.3f ms\n", c->phase_name[i], c->phase_ms[i]);
-      if (c->stats)
+      if (stats)
         fprintf(stderr, "[mochy]   words %llu  candidates %llu  table %llu  exact %llu  light %llu\n",
                 c->last_stats[0], c->last_stats[1], c->last_stats[2], c->last_stats[3],
                 c->last_stats[4]);
@@ -1279,12 +1282,12 @@ int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
   cudaStream_t st = ctx->stream;
   SplitArgs g;
   PhaseTimer timer(ctx);
-  if (timer.on && !ctx->stats) {
+  if (timer.stats && !ctx->stats) {
     void* p;
     MOCHY_TRY(dev_alloc(ctx, &p, 72 * sizeof(unsigned long long)));
     ctx->stats = (unsigned long long*)p;
   }
-  if (ctx->stats) MOCHY_CUDA(cudaMemsetAsync(ctx->stats, 0, 72 * sizeof(unsigned long long), st));
+  if (timer.stats) MOCHY_CUDA(cudaMemsetAsync(ctx->stats, 0, 72 * sizeof(unsigned long long), st));
   timer.mark("start");
   MOCHY_TRY(prepare_split(ctx));
   timer.mark("prepare");
@@ -1310,7 +1313,7 @@ int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
   g.dvedge = ctx->dvedge;
   g.dsize = ctx->dsize;
   g.cbits = ctx->sbits + 4 * ctx->wwords;
-  g.stats = timer.on ? ctx->stats : nullptr;
+  g.stats = timer.stats ? ctx->stats : nullptr;
   MOCHY_CUDA(cudaMemsetAsync(ctx->counters, 0, 16 * sizeof(int32_t), st));
   // open pairs
   {
