@@ -145,6 +145,24 @@ int mochy_count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t se
                         int64_t raw_h[MOCHY_N_H], int64_t raw_3h[MOCHY_N_3H],
                         double est_h[MOCHY_N_H], double est_3h[MOCHY_N_3H]);
 
+/* Sampled counts as mochy_count_sampled, written to caller-provided DEVICE
+ * arrays (d_raw_h[26], d_raw_3h[431] int64; d_est_h[26], d_est_3h[431] FP64),
+ * without allocating any device memory.  The paper has no counterpart: this
+ * is for callers that cannot allocate while they run, such as a process whose
+ * device memory is handed out by another runtime or pool, or a serving loop
+ * with a fixed memory reservation.  Its working memory is one fixed array
+ * inside the library (about 1.6 MB, held by every GPU that loads the library
+ * until the process exits), so MOCHY_A takes at most 65,536 samples per call
+ * (more returns MOCHY_E_UNSUPPORTED); MOCHY_A_PLUS has no limit.  The first
+ * call on a device looks the array up (cudaGetSymbolAddress) and should come
+ * before any stream capture.  All calls share the array: calls whose GPU work
+ * overlaps race, so run them one after another on the context's stream.
+ * MOCHY_A waits for its stream once (to size its work); the outputs are
+ * ready when the context's stream (mochy_stream) has completed. */
+int mochy_count_sampled_noalloc(mochy_ctx* ctx, int method, int64_t samples, uint64_t seed,
+                                int64_t* d_raw_h, int64_t* d_raw_3h, double* d_est_h,
+                                double* d_est_3h);
+
 /* One randomized hypergraph of the paper's null model into a new context
  * *out (same config): Chung-Lu on the incidence graph (Algorithm
  * "randomized_hypergraph_alg", Appendix "Randomized Hypergraphs") followed by

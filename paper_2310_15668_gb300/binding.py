@@ -29,6 +29,7 @@ EXPORTS = [
     "mochy_count_exact_subset", "mochy_count_sampled", "mochy_randomize", "mochy_profile",
     "mochy_motif_pattern", "mochy_stream", "mochy_device_bytes", "mochy_kernel_launches",
     "mochy_strerror", "mochy_last_error", "mochy_trace", "mochy_trace_read",
+    "mochy_count_sampled_noalloc",
 ]
 
 
@@ -86,6 +87,8 @@ def load_library(path: str = LIB_PATH):
             lib.mochy_profile.argtypes = [vp, i32, ctypes.c_uint64, vp, vp, vp, vp, vp, vp]
             lib.mochy_motif_pattern.argtypes = [ctypes.c_int, i32, vp]
             lib.mochy_trace.argtypes = [vp, ctypes.c_int]
+            lib.mochy_count_sampled_noalloc.argtypes = [vp, ctypes.c_int, i64, ctypes.c_uint64,
+                                                        vp, vp, vp, vp]
             lib.mochy_trace_read.argtypes = [vp, ctypes.c_char_p, i64]
             _lib = lib
     return _lib
@@ -186,6 +189,15 @@ def mochy_count_sampled(ctx: int, method: int, samples: int, seed: int):
     _check(load_library().mochy_count_sampled(ctx, method, samples, ctypes.c_uint64(seed), _p(rh),
                                               _p(r3), _p(eh), _p(e3)), "mochy_count_sampled")
     return rh, r3, eh, e3
+
+
+def mochy_count_sampled_noalloc(ctx: int, method: int, samples: int, seed: int, d_raw_h: int,
+                                d_raw_3h: int, d_est_h: int, d_est_3h: int) -> None:
+    """Sampled counts into caller-provided device arrays, with no device
+    allocation (for callers that cannot allocate while they run)."""
+    _check(load_library().mochy_count_sampled_noalloc(ctx, method, samples, ctypes.c_uint64(seed),
+                                                      d_raw_h, d_raw_3h, d_est_h, d_est_3h),
+           "mochy_count_sampled_noalloc")
 
 
 def mochy_randomize(ctx: int, seed: int, copy: int) -> int:

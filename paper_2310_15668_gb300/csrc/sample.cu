@@ -11,6 +11,8 @@
 // Random draws: Philox4x32-10 (Salmon et al., SC'11) on counter
 // (n_lo, n_hi, stream, 0) with key (seed_lo, seed_hi); the 64-bit output u
 // selects floor(u * range / 2^64).
+#include <mutex>
+
 #include "classify.cuh"
 #include "philox.cuh"
 
@@ -216,4 +218,155 @@ int count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t seed,
   return MOCHY_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Sampled counting without any device allocation.
+//
+// For callers that cannot allocate device memory while they run: a process
+// whose memory is handed out by another runtime or pool, a serving loop with
+// a fixed memory reservation, code that must not grow the context's footprint
+// between calls.  The working memory of this path (the motif histogram, the
+// drawn rows of MoCHy-A and their prefix sums) lives in one file-scope
+// __device__ array of kNoAllocBytes bytes, which every GPU that loads the
+// library holds until the process exits.  The first call on a device looks
+// up the array's device address (cudaGetSymbolAddress, with that device
+// current); that call should come before any stream capture.  All calls
+// share the array: each call clears what must start at zero, and calls whose
+// work overlaps on the GPU race on it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxSamplesA = 65536;   // MoCHy-A draws per call
+constexpr size_t kNoAllocHist = 432 * 8;
+constexpr size_t kNoAllocBytes = kNoAllocHist + 256 + 3 * (kNoAllocMaxSamplesA + 1) * 8;
+
+__global__ void __launch_bounds__(1024) k_noalloc_scan(const int64_t* __restrict__ in,
+                                                       int64_t* __restrict__ out, int64_t n) {
+  // exclusive scan of n values by one block, tile by tile
+  __shared__ int64_t ws[34];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = i < n ? in[i] : 0;
+    int64_t total;
+    const int64_t ex = block_scan_i64(v, ws, &total);
+    const int64_t c = carry;
+    if (i < n) out[i] = c + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry = c + total;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(512) k_noalloc_finish(
+    const unsigned long long* __restrict__ hist, const uint8_t* __restrict__ t2h,
+    const uint8_t* __restrict__ hopen, int method, double numer, double samples,
+    int64_t* __restrict__ raw_h, int64_t* __restrict__ raw_3h, double* __restrict__ est_h,
+    double* __restrict__ est_3h) {
+  __shared__ unsigned long long h[27];
+  if (threadIdx.x < 27) h[threadIdx.x] = 0ull;
+  __syncthreads();
+  for (int t = threadIdx.x + 1; t <= MOCHY_N_3H; t += blockDim.x) {
+    raw_3h[t - 1] = (int64_t)hist[t];
+    const double w = method == MOCHY_A ? 3.0 : (hopen[t2h[t]] ? 2.0 : 3.0);
+    est_3h[t - 1] = __ddiv_rn(__dmul_rn((double)hist[t], numer), __dmul_rn(w, samples));
+    atomicAdd(&h[t2h[t]], hist[t]);
+  }
+  __syncthreads();
+  if (threadIdx.x < MOCHY_N_H) {
+    const int id = threadIdx.x + 1;
+    raw_h[threadIdx.x] = (int64_t)h[id];
+    const double w = method == MOCHY_A ? 3.0 : (hopen[id] ? 2.0 : 3.0);
+    est_h[threadIdx.x] = __ddiv_rn(__dmul_rn((double)h[id], numer), __dmul_rn(w, samples));
+  }
+}
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch on the current device, looked up once.
+static int noalloc_scratch(int device, unsigned char** out) {
+  static std::mutex mu;
+  static unsigned char* addr[256] = {nullptr};
+  if (device < 0 || device >= 256) return fail(MOCHY_E_INVALID, "bad device ordinal");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
+    addr[device] = (unsigned char*)p;
+  }
+  *out = addr[device];
+  return MOCHY_OK;
+}
+
 }  // namespace mochy
+
+extern "C" int mochy_count_sampled_noalloc(mochy_ctx* ctx, int method, int64_t samples,
+                                           uint64_t seed, int64_t* d_raw_h, int64_t* d_raw_3h,
+                                           double* d_est_h, double* d_est_3h) {
+  using namespace mochy;
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  if (!d_raw_h || !d_raw_3h || !d_est_h || !d_est_3h) return fail(MOCHY_E_INVALID, "null output");
+  if (!ctx->projected) return fail(MOCHY_E_NOT_PROJECTED, "call mochy_project first");
+  if (method != MOCHY_A && method != MOCHY_A_PLUS) return fail(MOCHY_E_INVALID, "bad method");
+  if (samples <= 0) return fail(MOCHY_E_INVALID, "samples must be positive");
+  if (method == MOCHY_A && samples > kNoAllocMaxSamplesA)
+    return fail(MOCHY_E_UNSUPPORTED, "the allocation-free MoCHy-A takes at most 65536 samples "
+                                     "per call (its fixed working memory)");
+  if (method == MOCHY_A_PLUS && ctx->n_wedges == 0)
+    return fail(MOCHY_E_INVALID, "the hypergraph has no hyperwedge");
+  if (method == MOCHY_A && ctx->n_edges == 0)
+    return fail(MOCHY_E_INVALID, "the hypergraph has no hyperedge");
+  MOCHY_CUDA(cudaSetDevice(ctx->device));
+  unsigned char* base = nullptr;
+  MOCHY_TRY(noalloc_scratch(ctx->device, &base));
+  cudaStream_t st = ctx->stream;
+  unsigned long long* hist = (unsigned long long*)base;
+  int64_t* row = (int64_t*)(base + kNoAllocHist + 256);
+  int64_t* deg = row + (kNoAllocMaxSamplesA + 1);
+  int64_t* pre = deg + (kNoAllocMaxSamplesA + 1);
+  MOCHY_CUDA(cudaMemsetAsync(hist, 0, kNoAllocHist, st));
+  SampleArgs g;
+  g.n_edges = ctx->n_edges;
+  g.n_wedges = ctx->n_wedges;
+  g.eoff = ctx->eoff;
+  g.enode = ctx->enode;
+  g.noff = ctx->noff;
+  g.nadj = ctx->nadj;
+  g.ustart = ctx->ustart;
+  g.uprefix = ctx->uprefix;
+  g.lut3 = ctx->tables.lut3;
+  g.hist = hist;
+  g.theta = ctx->theta;
+  g.method = method;
+  g.seed = seed;
+  g.samples = samples;
+  g.item_prefix = nullptr;
+  g.sample_row = nullptr;
+  int64_t n_items = samples;
+  if (method == MOCHY_A) {
+    MOCHY_CUDA(cudaMemsetAsync(deg, 0, (size_t)(samples + 1) * 8, st));
+    k_draw_rows<<<ceil_div(samples, 256), 256, 0, st>>>(g, row, deg);
+    MOCHY_LAUNCHED();
+    k_noalloc_scan<<<1, 1024, 0, st>>>(deg, pre, samples + 1);
+    MOCHY_LAUNCHED();
+    MOCHY_CUDA(cudaMemcpyAsync(&n_items, pre + samples, 8, cudaMemcpyDeviceToHost, st));
+    MOCHY_CUDA(cudaStreamSynchronize(st));
+    g.item_prefix = pre;
+    g.sample_row = row;
+  }
+  if (n_items > 0) {
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n_items, kSampWarps),
+                                                      (int64_t)ctx->num_sms * 8);
+    k_sample_wedges<<<grid, kSampThreads, 0, st>>>(g, n_items);
+    MOCHY_LAUNCHED();
+  }
+  const double numer = method == MOCHY_A ? (double)ctx->n_edges : (double)ctx->n_wedges;
+  k_noalloc_finish<<<1, 512, 0, st>>>(hist, ctx->tables.t2h, ctx->tables.hopen, method, numer,
+                                      (double)samples, d_raw_h, d_raw_3h, d_est_h, d_est_3h);
+  MOCHY_LAUNCHED();
+  return MOCHY_OK;
+}
