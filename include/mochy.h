@@ -14,9 +14,9 @@
  * host thread at a time.
  *
  * Limits: at most 2^26 - 1 hyperedges, 2^31 - 1 nodes, 63 nodes per
- * hyperedge; exact counting needs at most 786,432 hyperedges (the per-row
- * adjacency of the line graph is staged in shared memory).  A call outside
- * these limits returns MOCHY_E_UNSUPPORTED.
+ * hyperedge; the per-hyperwedge scan kernel (exact_kernel = 1) needs at most
+ * 786,432 hyperedges (it stages a row's adjacency in shared memory).  A call
+ * outside these limits returns MOCHY_E_UNSUPPORTED.
  *
  * Motif ids: h-motifs are numbered 1..26, 3h-motifs 1..431 (arrays are
  * indexed id-1).  The paper's figures that fix the numbering are lost; the
@@ -183,6 +183,49 @@ int mochy_profile(mochy_ctx* ctx, int32_t n_random, uint64_t seed,
                   double sig_h[MOCHY_N_H], double cp_h[MOCHY_N_H],
                   double sig_3h[MOCHY_N_3H], double cp_3h[MOCHY_N_3H],
                   int64_t* counts_h, int64_t* counts_3h);
+
+/* Timings and sizes of a batched profile (mochy_profile_batch); times are
+ * device milliseconds summed over waves. */
+typedef struct {
+  double ms_generate;   /* inputs loaded, copies drawn, transformed and loaded */
+  double ms_project;    /* line graph of the union */
+  double ms_prepare;    /* split structures (dense index, bitmaps) */
+  double ms_count;      /* the one CUDA-graph launch of the counting kernels */
+  double ms_finish;     /* per-hypergraph counts, significance, CP, copy-out */
+  int64_t n_waves;      /* unions counted (1 unless memory forced a split) */
+  int64_t n_units;      /* hypergraphs counted: n_graphs * (1 + n_random) */
+  int64_t max_units_per_wave;
+  int64_t n_edges;      /* hyperedges of the unions (after duplicate removal) */
+  int64_t n_wedges;     /* hyperwedges of the unions */
+  int64_t instances;    /* connected triples counted, all hypergraphs */
+  int32_t dense_threshold;
+} mochy_batch_info;
+
+/* Significance and characteristic profiles (Eq. "significance", Eq. "cp",
+ * Section 3.1) of n_graphs hypergraphs at once: for graph g, exactly what
+ * mochy_profile computes for it with n_random copies and seed seeds[g].
+ * Graph g has n_nodes[g] >= 1 nodes and n_edges[g] hyperedges given as
+ * edge_offsets[g] (n_edges[g] + 1 entries from 0) and edge_nodes[g] (host
+ * arrays, copied; repeated hyperedges are dropped keeping the first).  The
+ * inputs and their randomized copies are generated on the device, as one
+ * disjoint union per wave (as many inputs as the configured memory budget,
+ * else 70% of the free device memory, allows), and every hypergraph of the
+ * union is counted exactly by one launch of a CUDA graph of persistent
+ * work-queue kernels.  Outputs (host, caller-allocated, each may be NULL):
+ * sig_h, cp_h [n_graphs][26]; sig_3h, cp_3h [n_graphs][431]; counts_h
+ * [n_graphs][1 + n_random][26] and counts_3h [n_graphs][1 + n_random][431]
+ * (the input first, then copies 0..); degenerate [n_graphs] (1 when all
+ * significances of h- or 3h-motifs are 0); info.  cfg gives theta, eps,
+ * device, budget and dense threshold (its stream is ignored: the batch runs
+ * on streams of its own; exact_kernel must be 0).  The environment variable
+ * MOCHY_BATCH_MAX_GRAPHS, when set to a positive number, caps the inputs per
+ * wave.  Returns MOCHY_W_DEGENERATE_CP when any graph is degenerate. */
+int mochy_profile_batch(const mochy_config* cfg, int32_t n_graphs, const int64_t* n_nodes,
+                        const int64_t* n_edges, const int64_t* const* edge_offsets,
+                        const int32_t* const* edge_nodes, int32_t n_random,
+                        const uint64_t* seeds, double* sig_h, double* cp_h, double* sig_3h,
+                        double* cp_3h, int64_t* counts_h, int64_t* counts_3h,
+                        int32_t* degenerate, mochy_batch_info* info);
 
 /* Region pattern of motif `id` (kind 2: h-motif, kind 3: 3h-motif): states
  * of regions (1)..(7) of Section 2.2 (0 empty, 1 at most theta nodes, 2 more;

@@ -29,7 +29,7 @@ EXPORTS = [
     "mochy_count_exact_subset", "mochy_count_sampled", "mochy_randomize", "mochy_profile",
     "mochy_motif_pattern", "mochy_stream", "mochy_device_bytes", "mochy_kernel_launches",
     "mochy_strerror", "mochy_last_error", "mochy_trace", "mochy_trace_read",
-    "mochy_count_sampled_noalloc",
+    "mochy_count_sampled_noalloc", "mochy_profile_batch",
 ]
 
 
@@ -44,6 +44,18 @@ class mochy_config(ctypes.Structure):
                 ("hbm_budget_bytes", ctypes.c_int64), ("device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("exact_kernel", ctypes.c_int32),
                 ("dense_threshold", ctypes.c_int32)]
+
+
+class mochy_batch_info(ctypes.Structure):
+    _fields_ = [("ms_generate", ctypes.c_double), ("ms_project", ctypes.c_double),
+                ("ms_prepare", ctypes.c_double), ("ms_count", ctypes.c_double),
+                ("ms_finish", ctypes.c_double), ("n_waves", ctypes.c_int64),
+                ("n_units", ctypes.c_int64), ("max_units_per_wave", ctypes.c_int64),
+                ("n_edges", ctypes.c_int64), ("n_wedges", ctypes.c_int64),
+                ("instances", ctypes.c_int64), ("dense_threshold", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 _lib = None
@@ -90,6 +102,9 @@ def load_library(path: str = LIB_PATH):
             lib.mochy_count_sampled_noalloc.argtypes = [vp, ctypes.c_int, i64, ctypes.c_uint64,
                                                         vp, vp, vp, vp]
             lib.mochy_trace_read.argtypes = [vp, ctypes.c_char_p, i64]
+            lib.mochy_profile_batch.argtypes = [ctypes.POINTER(mochy_config), i32, vp, vp, vp, vp,
+                                                i32, vp, vp, vp, vp, vp, vp, vp, vp,
+                                                ctypes.POINTER(mochy_batch_info)]
             _lib = lib
     return _lib
 
@@ -219,6 +234,36 @@ def mochy_profile(ctx: int, n_random: int, seed: int):
                 "mochy_profile")
     return dict(sig_h=sig_h, cp_h=cp_h, sig_3h=sig_3h, cp_3h=cp_3h, counts_h=ch, counts_3h=c3,
                 degenerate=rc == W_DEGENERATE_CP)
+
+
+def mochy_profile_batch(graphs, n_random: int, seeds, cfg: mochy_config | None = None):
+    """Profiles of several hypergraphs at once.  graphs: list of
+    (n_nodes, offsets, nodes); seeds: one per graph.  Returns
+    (sig_h [G,26], cp_h [G,26], sig_3h [G,431], cp_3h [G,431],
+    counts_h [G,1+R,26], counts_3h [G,1+R,431], degenerate [G], info dict)."""
+    G = len(graphs)
+    offs = [np.ascontiguousarray(o, dtype=np.int64) for _, o, _ in graphs]
+    nods = [np.ascontiguousarray(v, dtype=np.int32) for _, _, v in graphs]
+    nods = [v if v.size else np.zeros(1, np.int32) for v in nods]
+    n_nodes = np.array([int(n) for n, _, _ in graphs], np.int64)
+    n_edges = np.array([o.size - 1 for o in offs], np.int64)
+    po = (ctypes.c_void_p * max(G, 1))(*[o.ctypes.data for o in offs])
+    pn = (ctypes.c_void_p * max(G, 1))(*[v.ctypes.data for v in nods])
+    sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+    if sd.size == 0:
+        sd = np.zeros(1, np.uint64)
+    sig_h = np.zeros((G, N_H)); cp_h = np.zeros((G, N_H))
+    sig_3h = np.zeros((G, N_3H)); cp_3h = np.zeros((G, N_3H))
+    ch = np.zeros((G, max(n_random, 0) + 1, N_H), np.int64)
+    c3 = np.zeros((G, max(n_random, 0) + 1, N_3H), np.int64)
+    deg = np.zeros(max(G, 1), np.int32)
+    info = mochy_batch_info()
+    _check(load_library().mochy_profile_batch(
+        None if cfg is None else ctypes.byref(cfg), G, _p(n_nodes if G else np.zeros(1, np.int64)),
+        _p(n_edges if G else np.zeros(1, np.int64)), ctypes.cast(po, ctypes.c_void_p),
+        ctypes.cast(pn, ctypes.c_void_p), n_random, _p(sd), _p(sig_h), _p(cp_h), _p(sig_3h),
+        _p(cp_3h), _p(ch), _p(c3), _p(deg), ctypes.byref(info)), "mochy_profile_batch")
+    return sig_h, cp_h, sig_3h, cp_3h, ch, c3, deg[:G], info.as_dict()
 
 
 def mochy_motif_pattern(kind: int, motif_id: int) -> np.ndarray:

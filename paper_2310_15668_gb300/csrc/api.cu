@@ -114,6 +114,12 @@ void release_graph(mochy_ctx* ctx) {
     dev_free(ctx, ctx->voff, graph_bytes(ctx, 3));
     dev_free(ctx, ctx->vedge, graph_bytes(ctx, 4));
   }
+  if (ctx->d_nseg) dev_free(ctx, ctx->d_nseg, ctx->nseg_bytes);
+  ctx->d_nseg = nullptr;
+  ctx->nseg_bytes = 0;
+  ctx->n_units = 1;
+  ctx->h_nseg.clear();
+  ctx->h_eseg.clear();
   ctx->eoff = nullptr;
   ctx->enode = nullptr;
   ctx->esize = nullptr;

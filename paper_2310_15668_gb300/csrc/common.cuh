@@ -59,6 +59,17 @@ struct Tables {
   uint8_t* hopen = nullptr;   // [27]  h id -> 1 if open
 };
 
+// One hypergraph ("unit") of a batch counted as a disjoint union: where its
+// dense rows and heavy nodes sit in the split structures.  Its dense rows are
+// the dense indices [dbase, dbase + n); their bitmaps cover only the unit's
+// window of words [wlo, wlo + wn) and start at word dboff of dbits (2 wn words
+// a row); its heavy nodes are the heavy indices from hbase on, with bitmaps
+// of wn words from word nboff of nbits.  A lone hypergraph is one unit with
+// wlo = 0 and wn = the number of dense words.
+struct SegInfo {
+  int64_t dbase, dboff, hbase, nboff, wlo, wn;
+};
+
 // Scratch arena: grows on demand, freed with the context.
 struct Buffer {
   void* p = nullptr;
@@ -118,8 +129,21 @@ struct mochy_ctx {
   int64_t* dvoff = nullptr;         // [N+1] dense members of E_v ...
   int32_t* dvedge = nullptr;        // ... as dense indices, ascending
   uint8_t* dsize = nullptr;         // [n_dense] |e_k| of dense rows
-  size_t split_bytes = 0, nbits_bytes = 0, dinc_bytes = 0;
+  void* rest_block = nullptr;       // dbits .. dsize in one allocation
+  size_t split_bytes = 0, rest_bytes = 0, nbits_bytes = 0, dinc_bytes = 0;
   int32_t dense_thr_used = 0;
+
+  // disjoint union of n_units hypergraphs counted together (a batch): unit u
+  // owns the nodes [nseg[u], nseg[u+1]) and the hyperedges [eseg[u],
+  // eseg[u+1]); an exact count then fills one histogram per unit.  A lone
+  // hypergraph is one unit and keeps no arrays.
+  int32_t n_units = 1;
+  int64_t* d_nseg = nullptr;           // [n_units+1] on the device (then eseg)
+  size_t nseg_bytes = 0;
+  std::vector<int64_t> h_nseg, h_eseg; // [n_units+1] on the host
+  mochy::SegInfo* d_seg = nullptr;     // [n_units] (split structures)
+  int64_t* d_dbase = nullptr;          // [n_units+1] first dense index per unit
+  int64_t wmax = 0;                    // widest unit window, words
 
   // per-call device scratch
   unsigned long long* hist = nullptr;  // [432] 3h histogram (index = id)
@@ -166,6 +190,10 @@ void release_split(mochy_ctx* ctx);                                   // count_s
 int count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t seed,
                   unsigned long long* d_hist);                        // sample.cu
 int randomize_graph(mochy_ctx* src, uint64_t seed, uint32_t copy, mochy_ctx* dst);  // nullmodel.cu
+int pairs_to_hypergraph(mochy_ctx* work, uint32_t* node, uint32_t* edge, int64_t n_pairs,
+                        int64_t n_nodes, int64_t n_edges, mochy_ctx* dst);  // nullmodel.cu
+int bits_for(int64_t n);                                              // primitives.cu
+int count_split_graph(mochy_ctx* ctx, unsigned long long* d_hist, float* ms);  // count_split.cu
 int finish_counts(mochy_ctx* ctx, const unsigned long long* d_hist, int64_t* d_out_h,
                   int64_t* d_out_3h);                                 // profile.cu
 int scale_estimates(mochy_ctx* ctx, const int64_t* d_raw_h, const int64_t* d_raw_3h,
@@ -175,7 +203,24 @@ int significance_cp(mochy_ctx* ctx, const int64_t* d_counts_h, const int64_t* d_
                     int32_t n_random, double eps, double* d_out /* 4 vectors */,
                     int32_t* d_degenerate);                           // profile.cu
 
+int finish_counts_batch(mochy_ctx* ctx, const unsigned long long* d_hist, int n_hist,
+                        int64_t* d_out_h, int64_t* d_out_3h, int32_t* d_bad);  // profile.cu
+int significance_cp_batch(mochy_ctx* ctx, const int64_t* d_counts_h, const int64_t* d_counts_3h,
+                          int n_graphs, int32_t n_random, double eps, double* d_out,
+                          int32_t* d_degenerate);                     // profile.cu
+
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// largest u in [0, n) with b[u] <= x, for ascending b with b[0] <= x (with
+// equal bounds the later, non-empty range wins)
+__host__ __device__ __forceinline__ int seg_of(const int64_t* b, int n, int64_t x) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int m = (lo + hi) >> 1;
+    if (b[m] <= x) lo = m; else hi = m;
+  }
+  return lo;
+}
 
 // ---------------------------------------------------------------------------
 // Small device helpers.

@@ -108,7 +108,33 @@ struct SplitArgs {
   const int32_t* order;
   int64_t n_order;
   int32_t* queue;
+  // batch of disjoint hypergraphs: hist holds n_units histograms of 432
+  int32_t n_units;
+  const int64_t* nseg;       // [n_units+1] node ranges
+  const SegInfo* seg;        // [n_units]
 };
+
+// unit (hypergraph of a batch) of hyperedge a: the one owning its first node
+__device__ __forceinline__ int unit_of_edge(const SplitArgs& g, int64_t a) {
+  return seg_of(g.nseg, g.n_units, g.enode[g.eoff[a]]);
+}
+
+// Block-wide, between barriers: the shared histogram holds the counts of
+// unit `cur`; before rows of unit `next` are counted it is added to cur's
+// global histogram and cleared.  Ends with a barrier when it switches.
+__device__ __forceinline__ void switch_unit(unsigned long long* hist, unsigned long long* ghist,
+                                            int& cur, int next) {
+  if (next == cur) return;
+  for (int q = threadIdx.x; q < 432; q += blockDim.x) {
+    const unsigned long long v = hist[q];
+    if (v) {
+      atomicAdd(&ghist[(int64_t)cur * 432 + q], v);
+      hist[q] = 0ull;
+    }
+  }
+  cur = next;
+  __syncthreads();
+}
 
 __device__ __forceinline__ void load_lut(uint16_t* lut, const uint16_t* g, unsigned long long* hist) {
   for (int q = threadIdx.x; q < 432; q += blockDim.x) hist[q] = 0ull;
@@ -123,6 +149,89 @@ __device__ __forceinline__ void flush_hist(unsigned long long* g, const unsigned
 // ---------------------------------------------------------------------------
 // Open pairs: one warp per centre row.
 // ---------------------------------------------------------------------------
+// Open-pair counts of centre c (one warp) into hist.
+__device__ __forceinline__ void open_centre(const SplitArgs& g, int64_t c, unsigned long long* hist,
+                                            const uint16_t* lut, int32_t* key, int32_t* cnt) {
+  const int lane = threadIdx.x & 31;
+  constexpr int kPer = kTable / 32;
+  const int64_t rb = g.noff[c], re = g.noff[c + 1];
+  if (re - rb < 2) return;
+  const int A = (int)(g.eoff[c + 1] - g.eoff[c]);
+  for (int q = lane; q < kTable; q += 32) { key[q] = -1; cnt[q] = 0; }
+  __syncwarp();
+  bool overflow = false;
+  for (int64_t p = rb + lane; p < re; p += 32) {
+    const uint2 e = g.nadj[p];
+    const int x = entry_omega(e.y, A);
+    const int s = min(ent_size(e) - x, g.theta + 1);
+    const int k = (x << 8) | s;
+    unsigned h = ((unsigned)k * 2654435761u) >> 24;   // 8 bits
+    int probes = 0;
+    while (true) {
+      const int old = atomicCAS(&key[h], -1, k);
+      if (old == -1 || old == k) { atomicAdd(&cnt[h], 1); break; }
+      h = (h + 1) & (kTable - 1);
+      if (++probes >= kTable) { overflow = true; break; }
+    }
+  }
+  overflow = __any_sync(0xffffffffu, overflow);
+  __syncwarp();
+  if (overflow) {
+    // more distinct classes than the table holds: enumerate the pairs
+    for (int64_t p = rb; p < re; ++p) {
+      const uint2 ep = g.nadj[p];
+      const int x1 = entry_omega(ep.y, A);
+      for (int64_t q = p + 1 + lane; q < re; q += 32) {
+        const uint2 eq = g.nadj[q];
+        const int x2 = entry_omega(eq.y, A);
+        if (x1 + x2 > A) continue;
+        hadd(hist, lut[ternary_code(A, ent_size(ep), ent_size(eq), x1, 0, x2, 0, g.theta)], 1);
+      }
+    }
+    __syncwarp();
+    return;
+  }
+  // compact the used slots to the front, in place (each lane first reads
+  // its kPer consecutive slots)
+  int32_t rk[kPer], rc[kPer];
+  int mine = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    rk[q] = key[lane * kPer + q];
+    rc[q] = cnt[lane * kPer + q];
+    mine += rk[q] != -1 ? 1 : 0;
+  }
+  int incl = mine;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int o = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += o;
+  }
+  const int P = __shfl_sync(0xffffffffu, incl, 31);
+  __syncwarp();
+  int pos = incl - mine;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q)
+    if (rk[q] != -1) { key[pos] = rk[q]; cnt[pos] = rc[q]; ++pos; }
+  __syncwarp();
+  for (int i = lane; i < P; i += 32) {
+    const int x1 = key[i] >> 8, s1 = key[i] & 255;
+    const long long n1 = cnt[i];
+    for (int j = i; j < P; ++j) {
+      const int x2 = key[j] >> 8, s2 = key[j] & 255;
+      if (x1 + x2 > A) continue;
+      const long long n2 = cnt[j];
+      const long long n = i == j ? n1 * (n1 - 1) / 2 : n1 * n2;
+      if (n) hadd(hist, lut[ternary_code(A, x1 + s1, x2 + s2, x1, 0, x2, 0, g.theta)], n);
+    }
+  }
+  __syncwarp();
+}
+
+// One warp per centre row.  For a batch (kSeg) the block takes 8 consecutive
+// centres at a time and counts into the shared histogram of the unit of the
+// first; a centre of another unit (at a unit boundary) adds to its unit's
+// global histogram directly.
+template <bool kSeg>
 __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
   __shared__ unsigned long long hist[432];
   __shared__ uint16_t lut[2192];
@@ -130,86 +239,29 @@ __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
   __shared__ int32_t tcnt[kOpenWarps][kTable];
   load_lut(lut, g.lut3, hist);
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
   int32_t* key = tkey[warp];
   int32_t* cnt = tcnt[warp];
-  constexpr int kPer = kTable / 32;
   const int64_t nw = (int64_t)gridDim.x * kOpenWarps;
-  for (int64_t c = (int64_t)blockIdx.x * kOpenWarps + warp; c < g.n_edges; c += nw) {
-    const int64_t rb = g.noff[c], re = g.noff[c + 1];
-    if (re - rb < 2) continue;
-    const int A = (int)(g.eoff[c + 1] - g.eoff[c]);
-    for (int q = lane; q < kTable; q += 32) { key[q] = -1; cnt[q] = 0; }
-    __syncwarp();
-    bool overflow = false;
-    for (int64_t p = rb + lane; p < re; p += 32) {
-      const uint2 e = g.nadj[p];
-      const int x = entry_omega(e.y, A);
-      const int s = min(ent_size(e) - x, g.theta + 1);
-      const int k = (x << 8) | s;
-      unsigned h = ((unsigned)k * 2654435761u) >> 24;   // 8 bits
-      int probes = 0;
-      while (true) {
-        const int old = atomicCAS(&key[h], -1, k);
-        if (old == -1 || old == k) { atomicAdd(&cnt[h], 1); break; }
-        h = (h + 1) & (kTable - 1);
-        if (++probes >= kTable) { overflow = true; break; }
-      }
+  if (!kSeg) {
+    for (int64_t c = (int64_t)blockIdx.x * kOpenWarps + warp; c < g.n_edges; c += nw)
+      open_centre(g, c, hist, lut, key, cnt);
+    __syncthreads();
+    flush_hist(g.hist, hist);
+    return;
+  }
+  int cur = 0;
+  for (int64_t c0 = (int64_t)blockIdx.x * kOpenWarps; c0 < g.n_edges; c0 += nw) {
+    __syncthreads();
+    switch_unit(hist, g.hist, cur, unit_of_edge(g, c0));
+    const int64_t c = c0 + warp;
+    if (c < g.n_edges) {
+      const int u = unit_of_edge(g, c);
+      open_centre(g, c, u == cur ? hist : g.hist + (int64_t)u * 432, lut, key, cnt);
     }
-    overflow = __any_sync(0xffffffffu, overflow);
-    __syncwarp();
-    if (overflow) {
-      // more distinct classes than the table holds: enumerate the pairs
-      for (int64_t p = rb; p < re; ++p) {
-        const uint2 ep = g.nadj[p];
-        const int x1 = entry_omega(ep.y, A);
-        for (int64_t q = p + 1 + lane; q < re; q += 32) {
-          const uint2 eq = g.nadj[q];
-          const int x2 = entry_omega(eq.y, A);
-          if (x1 + x2 > A) continue;
-          hadd(hist, lut[ternary_code(A, ent_size(ep), ent_size(eq), x1, 0, x2, 0, g.theta)], 1);
-        }
-      }
-      __syncwarp();
-      continue;
-    }
-    // compact the used slots to the front, in place (each lane first reads
-    // its kPer consecutive slots)
-    int32_t rk[kPer], rc[kPer];
-    int mine = 0;
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      rk[q] = key[lane * kPer + q];
-      rc[q] = cnt[lane * kPer + q];
-      mine += rk[q] != -1 ? 1 : 0;
-    }
-    int incl = mine;
-    for (int d = 1; d < 32; d <<= 1) {
-      const int o = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += o;
-    }
-    const int P = __shfl_sync(0xffffffffu, incl, 31);
-    __syncwarp();
-    int pos = incl - mine;
-#pragma unroll
-    for (int q = 0; q < kPer; ++q)
-      if (rk[q] != -1) { key[pos] = rk[q]; cnt[pos] = rc[q]; ++pos; }
-    __syncwarp();
-    for (int i = lane; i < P; i += 32) {
-      const int x1 = key[i] >> 8, s1 = key[i] & 255;
-      const long long n1 = cnt[i];
-      for (int j = i; j < P; ++j) {
-        const int x2 = key[j] >> 8, s2 = key[j] & 255;
-        if (x1 + x2 > A) continue;
-        const long long n2 = cnt[j];
-        const long long n = i == j ? n1 * (n1 - 1) / 2 : n1 * n2;
-        if (n) hadd(hist, lut[ternary_code(A, x1 + s1, x2 + s2, x1, 0, x2, 0, g.theta)], n);
-      }
-    }
-    __syncwarp();
   }
   __syncthreads();
-  flush_hist(g.hist, hist);
+  flush_hist(g.hist + (int64_t)cur * 432, hist);
 }
 
 // ---------------------------------------------------------------------------
@@ -363,7 +415,7 @@ __constant__ int c_pop[7][5] = {
     {0, 2, 1, 3, 4}, {1, 1, 1, 3, 4}, {0, 0, 2, 2, 5}};
 constexpr int kPopBins = 28;   // total bins, counted two per register
 
-template <bool kTheta1>
+template <bool kTheta1, bool kSeg>
 __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* hist = (unsigned long long*)smem;
@@ -374,8 +426,10 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
   const int64_t W = g.wwords;
   __shared__ int64_t slot_s;
   __shared__ int64_t row_next;
+  __shared__ int unit_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpScratch& me = ws[warp];
+  int cur = 0;   // unit whose counts the shared histogram holds (kSeg)
   load_lut(lut, g.lut3, hist);
   for (int q = lane; q < kCombo * kCeff; q += 32) me.table[q] = 0u;
   me.dirty[lane] = 0u;
@@ -386,20 +440,38 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
   const uint32_t* P3 = g.sbits + 3 * W;
   while (true) {
     __syncthreads();
-    if (threadIdx.x == 0) slot_s = atomicAdd(g.queue, 1);
+    if (threadIdx.x == 0) {
+      slot_s = atomicAdd(g.queue, 1);
+      if (kSeg && slot_s < g.n_order) unit_s = unit_of_edge(g, g.order[slot_s]);
+    }
     __syncthreads();
     const int64_t slot = slot_s;
     if (slot >= g.n_order) break;
+    // the window of dense words of this row's hypergraph (all of them when
+    // there is one); bitmaps are indexed by word - WLO
+    int64_t WLO = 0, WHI = W, WN = W, hbase = 0, dboff = 0, dbase = 0;
+    const uint32_t* NB = g.nbits;
+    if (kSeg) {
+      switch_unit(hist, g.hist, cur, unit_s);
+      const SegInfo sg = g.seg[cur];
+      WLO = sg.wlo;
+      WN = sg.wn;
+      WHI = sg.wlo + sg.wn;
+      hbase = sg.hbase;
+      dboff = sg.dboff;
+      dbase = sg.dbase;
+      NB = g.nbits + sg.nboff;
+    }
     const int64_t a = g.order[slot];
     const int ad = g.dense_idx[a];
     const int64_t rb = g.noff[a], re = g.noff[a + 1];
     const int A = (int)(g.eoff[a + 1] - g.eoff[a]);
     if (threadIdx.x < A) anodes[threadIdx.x] = g.enode[g.eoff[a] + threadIdx.x];
-    for (int64_t q = threadIdx.x; q < W; q += kDThreads) A1[q] = 0u;
+    for (int64_t q = threadIdx.x; q < WN; q += kDThreads) A1[q] = 0u;
     __syncthreads();
     for (int64_t p = rb + threadIdx.x; p < re; p += kDThreads) {
       const int kd = g.dense_idx[ent_id(g.nadj[p])];
-      if (kd >= 0) atomicOr(&A1[kd >> 5], 1u << (kd & 31));
+      if (kd >= 0) atomicOr(&A1[(kd >> 5) - WLO], 1u << (kd & 31));
     }
     __syncthreads();
     if (threadIdx.x == 0) row_next = rb;
@@ -436,7 +508,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         for (int gg = 0; gg < 3; ++gg) {
           const bool mine = grp == gg && hv >= 0;
           const unsigned bal = __ballot_sync(0xffffffffu, mine);
-          if (mine) me.hidx[gg][me.n[gg] + __popc(bal & ((1u << lane) - 1u))] = hv;
+          if (mine) me.hidx[gg][me.n[gg] + __popc(bal & ((1u << lane) - 1u))] = hv - (int)hbase;
           __syncwarp();
           if (lane == 0) me.n[gg] += __popc(bal);
           __syncwarp();
@@ -453,7 +525,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         __syncwarp();
       }
       const int nA = me.n[0], nB = me.n[1], nT = me.n[2], nL = me.n[3];
-      const uint32_t* B1 = g.dbits + (int64_t)bd * 2 * W;
+      const uint32_t* B1 = g.dbits + dboff + (int64_t)(bd - dbase) * 2 * WN;
       // per-lane counters: 14 pairs of 16-bit bins (theta = 1) or 10 bins
       uint32_t cnt[14];
 #pragma unroll
@@ -507,18 +579,18 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       long long t_words0 = g.stats ? clock64() : 0;
       // uniform loop: every lane runs every iteration (lanes past the end see
       // an empty word), so the warp stays converged
-      for (int64_t w0 = fw; w0 < W; w0 += 32) {
-        const bool inr = w0 + lane < W;
-        const int64_t w = inr ? w0 + lane : W - 1;
-        uint32_t m = inr ? (A1[w] & __ldg(&B1[w])) : 0u;
+      for (int64_t w0 = fw; w0 < WHI; w0 += 32) {
+        const bool inr = w0 + lane < WHI;
+        const int64_t w = inr ? w0 + lane : WHI - 1;
+        uint32_t m = inr ? (A1[w - WLO] & __ldg(&B1[w - WLO])) : 0u;
         if (w == fw) m &= 0xffffffffu << (first & 31);
         uint32_t a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0, t0 = 0, t1 = 0, t2 = 0, ovf = 0;
         for (int h = 0; h < nA; ++h)
-          slice_add(a0, a1, a2, ovf, __ldg(&g.nbits[(int64_t)me.hidx[0][h] * W + w]));
+          slice_add(a0, a1, a2, ovf, __ldg(&NB[(int64_t)me.hidx[0][h] * WN + (w - WLO)]));
         for (int h = 0; h < nB; ++h)
-          slice_add(b0, b1, b2, ovf, __ldg(&g.nbits[(int64_t)me.hidx[1][h] * W + w]));
+          slice_add(b0, b1, b2, ovf, __ldg(&NB[(int64_t)me.hidx[1][h] * WN + (w - WLO)]));
         for (int h = 0; h < nT; ++h)
-          slice_add(t0, t1, t2, ovf, __ldg(&g.nbits[(int64_t)me.hidx[2][h] * W + w]));
+          slice_add(t0, t1, t2, ovf, __ldg(&NB[(int64_t)me.hidx[2][h] * WN + (w - WLO)]));
         // light nodes with a dense index in this iteration's 32 words
         const int64_t hi64 = (w0 + 32) * 32;
         const int32_t hi = hi64 < 0x7fffffff ? (int32_t)hi64 : 0x7fffffff;
@@ -692,7 +764,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           st_exact += __shfl_xor_sync(0xffffffffu, st_exact, d);
         }
         if (lane == 0) {
-          atomicAdd(&g.stats[0], (unsigned long long)(W - fw));
+          atomicAdd(&g.stats[0], (unsigned long long)(WHI - fw));
           atomicAdd(&g.stats[1], st_cand);
           atomicAdd(&g.stats[2], st_table);
           atomicAdd(&g.stats[3], st_exact);
@@ -752,7 +824,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
     }
   }
   __syncthreads();
-  flush_hist(g.hist, hist);
+  flush_hist(g.hist + (int64_t)cur * 432, hist);
 }
 
 // ---------------------------------------------------------------------------
@@ -761,6 +833,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
 // Shared layout: hist | lut | anodes[64] | per-warp bnodes[64] |
 // key[D] | w1[D] | size[D] | didx[D]
 // ---------------------------------------------------------------------------
+template <bool kSeg>
 __global__ void __launch_bounds__(kThreads) k_sparse_triangles(SplitArgs g, int max_deg) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* hist = (unsigned long long*)smem;
@@ -772,16 +845,30 @@ __global__ void __launch_bounds__(kThreads) k_sparse_triangles(SplitArgs g, int 
   int32_t* sdi = (int32_t*)(sw1 + max_deg);
   uint8_t* ssz = (uint8_t*)(sdi + max_deg);
   __shared__ int64_t slot_s;
+  __shared__ int unit_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int32_t* bnodes = bnodes_all + 64 * warp;
   const int64_t W = g.wwords;
+  int cur = 0;   // unit whose counts the shared histogram holds (kSeg)
   load_lut(lut, g.lut3, hist);
   while (true) {
     __syncthreads();
-    if (threadIdx.x == 0) slot_s = atomicAdd(g.queue, 1);
+    if (threadIdx.x == 0) {
+      slot_s = atomicAdd(g.queue, 1);
+      if (kSeg && slot_s < g.n_order) unit_s = unit_of_edge(g, g.order[slot_s]);
+    }
     __syncthreads();
     const int64_t slot = slot_s;
     if (slot >= g.n_order) break;
+    int64_t WLO = 0, WN = W, dboff = 0, dbase = 0;
+    if (kSeg) {
+      switch_unit(hist, g.hist, cur, unit_s);
+      const SegInfo sg = g.seg[cur];
+      WLO = sg.wlo;
+      WN = sg.wn;
+      dboff = sg.dboff;
+      dbase = sg.dbase;
+    }
     const int64_t a = g.order[slot];
     const int64_t rb = g.noff[a], re = g.noff[a + 1];
     const int deg = (int)(re - rb);
@@ -808,17 +895,17 @@ __global__ void __launch_bounds__(kThreads) k_sparse_triangles(SplitArgs g, int 
       __syncwarp();
       if (bd >= 0) {
         // b dense: every k after b is dense with a larger dense index
-        const uint32_t* B1 = g.dbits + (int64_t)bd * 2 * W;
-        const uint32_t* B2 = B1 + W;
+        const uint32_t* B1 = g.dbits + dboff + (int64_t)(bd - dbase) * 2 * WN;
+        const uint32_t* B2 = B1 + WN;
         for (int q = lane; q < deg; q += 32) {
           const int kd = sdi[q];
           if (kd <= bd) continue;
           const uint32_t bit = 1u << (kd & 31);
-          if (!(__ldg(&B1[kd >> 5]) & bit)) continue;
+          if (!(__ldg(&B1[(kd >> 5) - WLO]) & bit)) continue;
           const int64_t k = skey[q];
           const int C = ssz[q];
           int y = 1;
-          if (__ldg(&B2[kd >> 5]) & bit) {
+          if (__ldg(&B2[(kd >> 5) - WLO]) & bit) {
             const int64_t kb = g.eoff[k];
             y = sorted_overlap(bnodes, B, g.enode + kb, C);
           }
@@ -861,7 +948,7 @@ __global__ void __launch_bounds__(kThreads) k_sparse_triangles(SplitArgs g, int 
     }
   }
   __syncthreads();
-  flush_hist(g.hist, hist);
+  flush_hist(g.hist + (int64_t)cur * 432, hist);
 }
 
 // ---------------------------------------------------------------------------
@@ -899,21 +986,53 @@ __global__ void k_dense_reindex(int64_t n_dense, const int32_t* __restrict__ dro
   if (r < n_dense) didx[drow[r]] = (int32_t)r;
 }
 
-__global__ void k_dense_bits(int64_t n_dense, int64_t W, const int32_t* __restrict__ drow,
+// unit of each dense row (rows of a batch)
+__global__ void k_dense_units(int64_t n_dense, const int32_t* __restrict__ drow,
+                              const int64_t* __restrict__ eoff, const int32_t* __restrict__ enode,
+                              const int64_t* __restrict__ nseg, int n_units,
+                              uint32_t* __restrict__ unit) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n_dense) unit[r] = (uint32_t)seg_of(nseg, n_units, enode[eoff[drow[r]]]);
+}
+
+// first index of each unit in an array of units sorted ascending: out[u] =
+// number of entries below u, u = 0..n_units
+__global__ void k_unit_starts(int64_t n, const uint32_t* __restrict__ unit, int n_units,
+                              int64_t* __restrict__ out) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u > n_units) return;
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t m = (lo + hi) >> 1;
+    if (unit[m] < (uint32_t)u) lo = m + 1; else hi = m;
+  }
+  out[u] = lo;
+}
+
+__global__ void k_gather_at(int n, const int64_t* __restrict__ src, const int64_t* __restrict__ at,
+                            int64_t* __restrict__ out) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n) out[u] = src[at[u]];
+}
+
+__global__ void k_dense_bits(int64_t n_dense, const SegInfo* __restrict__ seg,
+                             const int64_t* __restrict__ dbase, int n_units,
+                             const int32_t* __restrict__ drow,
                              const int64_t* __restrict__ eoff, const int64_t* __restrict__ noff,
                              const uint2* __restrict__ nadj, const int32_t* __restrict__ didx,
                              uint32_t* __restrict__ dbits) {
   for (int64_t r = blockIdx.x; r < n_dense; r += gridDim.x) {
+    const SegInfo sg = seg[seg_of(dbase, n_units, r)];
     const int64_t b = drow[r];
     const int B = (int)(eoff[b + 1] - eoff[b]);
-    uint32_t* B1 = dbits + r * 2 * W;
-    uint32_t* B2 = B1 + W;
+    uint32_t* B1 = dbits + sg.dboff + (r - sg.dbase) * 2 * sg.wn;
+    uint32_t* B2 = B1 + sg.wn;
     for (int64_t p = noff[b] + threadIdx.x; p < noff[b + 1]; p += blockDim.x) {
       const uint2 e = nadj[p];
       const int kd = didx[ent_id(e)];
       if (kd < 0) continue;
-      atomicOr(&B1[kd >> 5], 1u << (kd & 31));
-      if (entry_omega(e.y, B) >= 2) atomicOr(&B2[kd >> 5], 1u << (kd & 31));
+      atomicOr(&B1[(kd >> 5) - sg.wlo], 1u << (kd & 31));
+      if (entry_omega(e.y, B) >= 2) atomicOr(&B2[(kd >> 5) - sg.wlo], 1u << (kd & 31));
     }
   }
 }
@@ -937,7 +1056,9 @@ __global__ void k_heavy_index(int64_t N, const int64_t* __restrict__ flag,
   if (v < N) hidx[v] = flag[v] ? (int32_t)pos[v] : -1;
 }
 
-__global__ void k_heavy_bits(int64_t N, int64_t W, const int64_t* __restrict__ voff,
+__global__ void k_heavy_bits(int64_t N, const SegInfo* __restrict__ seg,
+                             const int64_t* __restrict__ nseg, int n_units,
+                             const int64_t* __restrict__ voff,
                              const int32_t* __restrict__ vedge, const int32_t* __restrict__ didx,
                              const int32_t* __restrict__ hidx, uint32_t* __restrict__ nbits) {
   const int64_t v = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
@@ -945,10 +1066,11 @@ __global__ void k_heavy_bits(int64_t N, int64_t W, const int64_t* __restrict__ v
   if (v >= N) return;
   const int h = hidx[v];
   if (h < 0) return;
-  uint32_t* bits = nbits + (int64_t)h * W;
+  const SegInfo sg = seg[seg_of(nseg, n_units, v)];
+  uint32_t* bits = nbits + sg.nboff + (h - sg.hbase) * sg.wn;
   for (int64_t q = voff[v] + lane; q < voff[v + 1]; q += 32) {
     const int kd = didx[vedge[q]];
-    if (kd >= 0) atomicOr(&bits[kd >> 5], 1u << (kd & 31));
+    if (kd >= 0) atomicOr(&bits[(kd >> 5) - sg.wlo], 1u << (kd & 31));
   }
 }
 
@@ -1046,6 +1168,7 @@ void release_split(mochy_ctx* ctx) {
   if (!ctx->split_ready && !ctx->dense_idx) return;
   cudaStreamSynchronize(ctx->stream);
   if (ctx->dense_idx) dev_free(ctx, ctx->dense_idx, ctx->split_bytes);
+  if (ctx->rest_block) dev_free(ctx, ctx->rest_block, ctx->rest_bytes);
   if (ctx->nbits) dev_free(ctx, ctx->nbits, ctx->nbits_bytes);
   if (ctx->dvoff) dev_free(ctx, ctx->dvoff, ctx->dinc_bytes);
   ctx->dvoff = nullptr;
@@ -1059,9 +1182,12 @@ void release_split(mochy_ctx* ctx) {
   ctx->sbits = nullptr;
   ctx->dense_order = ctx->sparse_order = nullptr;
   ctx->dsize = nullptr;
-  ctx->split_bytes = 0;
+  ctx->d_seg = nullptr;
+  ctx->d_dbase = nullptr;
+  ctx->rest_block = nullptr;
+  ctx->split_bytes = ctx->rest_bytes = 0;
   ctx->split_ready = false;
-  ctx->n_dense = ctx->n_sparse = ctx->n_heavy = ctx->wwords = 0;
+  ctx->n_dense = ctx->n_sparse = ctx->n_heavy = ctx->wwords = ctx->wmax = 0;
 }
 
 int choose_dense_threshold(mochy_ctx* ctx);   // tune.cu
@@ -1077,6 +1203,7 @@ size_t sparse_smem_bytes(int max_deg) {
 int prepare_split(mochy_ctx* ctx) {
   if (ctx->split_ready) return MOCHY_OK;
   const int64_t E = ctx->n_edges, N = ctx->n_nodes;
+  const int U = ctx->n_units;
   cudaStream_t st = ctx->stream;
   const int thr = ctx->dense_thr > 0 ? ctx->dense_thr : choose_dense_threshold(ctx);
   if (thr <= 0) return thr < 0 ? thr : fail(MOCHY_E_UNSUPPORTED, "no usable dense threshold");
@@ -1093,76 +1220,144 @@ int prepare_split(mochy_ctx* ctx) {
   int64_t n_dense = 0;
   MOCHY_CUDA(cudaMemcpyAsync(&n_dense, pos + E, 8, cudaMemcpyDeviceToHost, st));
   MOCHY_CUDA(cudaStreamSynchronize(st));
-  const int64_t W = std::max<int64_t>((n_dense + 31) / 32, 1);
-  if (dense_smem_bytes(W) + 1024 > ctx->smem_optin)
-    return fail(MOCHY_E_UNSUPPORTED, "too many dense rows for the shared-memory bitmap");
-  // heavy nodes need dense indices first: allocate everything in one block
-  // (sizes of the heavy part are bounded by N)
+  const int64_t W = std::max<int64_t>((n_dense + 31) / 32, 1);   // words of the size planes
+  // the dense index, dense rows and unit tables first; the bitmaps are sized
+  // once the units' dense ranges are known
   const int64_t nd1 = std::max<int64_t>(n_dense, 1);
-  size_t off_idx = 0;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t b_didx = al((size_t)std::max<int64_t>(E, 1) * 4);
   const size_t b_drow = al((size_t)nd1 * 4);
-  const size_t b_dbits = al((size_t)nd1 * 2 * W * 4);
   const size_t b_hidx = al((size_t)std::max<int64_t>(N, 1) * 4);
   const size_t b_sbits = al((size_t)(4 + kClasses) * W * 4);
   const size_t b_ord = al((size_t)std::max<int64_t>(E, 1) * 4);
   const size_t b_dsize = al((size_t)nd1);
-  const size_t head = b_didx + b_drow + b_dbits + b_hidx + b_sbits + 2 * b_ord + b_dsize;
-  (void)off_idx;
-  // count heavy nodes before sizing their bitmaps: needs dense_idx, so build
-  // the head block first
-  void* p;
-  MOCHY_TRY(dev_alloc(ctx, &p, head));
-  char* base = (char*)p;
-  ctx->dense_idx = (int32_t*)base;
-  ctx->dense_row = (int32_t*)(base + b_didx);
-  ctx->dbits = (uint32_t*)(base + b_didx + b_drow);
-  ctx->heavy_idx = (int32_t*)(base + b_didx + b_drow + b_dbits);
-  ctx->sbits = (uint32_t*)(base + b_didx + b_drow + b_dbits + b_hidx);
-  ctx->dense_order = (int32_t*)(base + b_didx + b_drow + b_dbits + b_hidx + b_sbits);
-  ctx->sparse_order = (int32_t*)((char*)ctx->dense_order + b_ord);
-  ctx->dsize = (uint8_t*)((char*)ctx->sparse_order + b_ord);
-  ctx->split_bytes = head;
+  const size_t b_seg = al((size_t)U * sizeof(SegInfo));
+  const size_t b_dbase = al((size_t)(U + 1) * 8);
+  void* p0;
+  MOCHY_TRY(dev_alloc(ctx, &p0, b_didx + b_drow + b_seg + b_dbase));
+  ctx->dense_idx = (int32_t*)p0;
+  ctx->dense_row = (int32_t*)((char*)p0 + b_didx);
+  ctx->d_seg = (SegInfo*)((char*)p0 + b_didx + b_drow);
+  ctx->d_dbase = (int64_t*)((char*)p0 + b_didx + b_drow + b_seg);
+  ctx->split_bytes = b_didx + b_drow + b_seg + b_dbase;
   k_dense_index<<<ceil_div(E, 256), 256, 0, st>>>(E, flag, pos, ctx->dense_idx, ctx->dense_row);
   MOCHY_LAUNCHED();
   // dense indices in ascending line degree (ties by id): triangles among
-  // dense rows are then found from their lowest-degree member
-  if (n_dense > 1) {
+  // dense rows are then found from their lowest-degree member.  In a batch
+  // the rows are grouped by unit first (stable), so each unit's dense rows
+  // are one range of indices.
+  std::vector<int64_t> hdb((size_t)U + 1, 0);
+  hdb[U] = n_dense;
+  if (n_dense > 0) {
     void* kt;
     MOCHY_TRY(scratch(ctx, 2, (size_t)n_dense * 4, &kt));
-    k_dense_keys<<<ceil_div(n_dense, 256), 256, 0, st>>>(n_dense, ctx->dense_row, ctx->noff,
-                                                         (uint32_t*)kt);
-    MOCHY_LAUNCHED();
-    MOCHY_TRY(radix_sort_pairs_u32(ctx, (uint32_t*)kt, (uint32_t*)ctx->dense_row, n_dense, 32));
+    if (n_dense > 1) {
+      k_dense_keys<<<ceil_div(n_dense, 256), 256, 0, st>>>(n_dense, ctx->dense_row, ctx->noff,
+                                                           (uint32_t*)kt);
+      MOCHY_LAUNCHED();
+      MOCHY_TRY(radix_sort_pairs_u32(ctx, (uint32_t*)kt, (uint32_t*)ctx->dense_row, n_dense, 32));
+    }
+    if (U > 1) {
+      k_dense_units<<<ceil_div(n_dense, 256), 256, 0, st>>>(n_dense, ctx->dense_row, ctx->eoff,
+                                                            ctx->enode, ctx->d_nseg, U,
+                                                            (uint32_t*)kt);
+      MOCHY_LAUNCHED();
+      MOCHY_TRY(radix_sort_pairs_u32(ctx, (uint32_t*)kt, (uint32_t*)ctx->dense_row, n_dense,
+                                     bits_for(U)));
+      k_unit_starts<<<ceil_div(U + 1, 256), 256, 0, st>>>(n_dense, (const uint32_t*)kt, U,
+                                                           ctx->d_dbase);
+      MOCHY_LAUNCHED();
+      MOCHY_CUDA(cudaMemcpyAsync(hdb.data(), ctx->d_dbase, (size_t)(U + 1) * 8,
+                                 cudaMemcpyDeviceToHost, st));
+    }
     k_dense_reindex<<<ceil_div(n_dense, 256), 256, 0, st>>>(n_dense, ctx->dense_row,
                                                             ctx->dense_idx);
     MOCHY_LAUNCHED();
+    MOCHY_CUDA(cudaStreamSynchronize(st));
   }
-  MOCHY_CUDA(cudaMemsetAsync(ctx->dbits, 0, (size_t)nd1 * 2 * W * 4, st));
+  // each unit's window of dense words and the place of its bitmaps
+  std::vector<SegInfo> seg((size_t)U);
+  int64_t dwords = 0, wmax = 0;
+  for (int u = 0; u < U; ++u) {
+    SegInfo& sg = seg[u];
+    const int64_t nd = hdb[u + 1] - hdb[u];
+    sg.dbase = hdb[u];
+    sg.wlo = hdb[u] >> 5;
+    sg.wn = nd > 0 ? ((hdb[u + 1] + 31) >> 5) - sg.wlo : 0;
+    sg.dboff = dwords;
+    dwords += nd * 2 * sg.wn;
+    sg.hbase = sg.nboff = 0;
+    wmax = std::max(wmax, sg.wn);
+  }
+  if (dense_smem_bytes(wmax) + 1024 > ctx->smem_optin) {
+    release_split(ctx);
+    return fail(MOCHY_E_UNSUPPORTED, "too many dense rows for the shared-memory bitmap");
+  }
+  const size_t b_dbits = al((size_t)std::max<int64_t>(dwords, 1) * 4);
+  const size_t rest = b_dbits + b_hidx + b_sbits + 2 * b_ord + b_dsize;
+  void* p1;
+  {
+    const int rc = dev_alloc(ctx, &p1, rest);
+    if (rc < 0) {
+      release_split(ctx);
+      return rc;
+    }
+  }
+  ctx->rest_block = p1;
+  ctx->rest_bytes = rest;
+  char* base = (char*)p1;
+  ctx->dbits = (uint32_t*)base;
+  ctx->heavy_idx = (int32_t*)(base + b_dbits);
+  ctx->sbits = (uint32_t*)(base + b_dbits + b_hidx);
+  ctx->dense_order = (int32_t*)(base + b_dbits + b_hidx + b_sbits);
+  ctx->sparse_order = (int32_t*)((char*)ctx->dense_order + b_ord);
+  ctx->dsize = (uint8_t*)((char*)ctx->sparse_order + b_ord);
+  if (U == 1 || n_dense == 0)
+    MOCHY_CUDA(cudaMemcpyAsync(ctx->d_dbase, hdb.data(), (size_t)(U + 1) * 8,
+                               cudaMemcpyHostToDevice, st));
+  MOCHY_CUDA(cudaMemcpyAsync(ctx->d_seg, seg.data(), (size_t)U * sizeof(SegInfo),
+                             cudaMemcpyHostToDevice, st));
+  MOCHY_CUDA(cudaMemsetAsync(ctx->dbits, 0, b_dbits, st));
   MOCHY_CUDA(cudaMemsetAsync(ctx->sbits, 0, (size_t)(4 + kClasses) * W * 4, st));
   if (n_dense > 0) {
     k_dense_bits<<<(unsigned)std::min<int64_t>(n_dense, 1 << 16), 256, 0, st>>>(
-        n_dense, W, ctx->dense_row, ctx->eoff, ctx->noff, ctx->nadj, ctx->dense_idx, ctx->dbits);
+        n_dense, ctx->d_seg, ctx->d_dbase, U, ctx->dense_row, ctx->eoff, ctx->noff, ctx->nadj,
+        ctx->dense_idx, ctx->dbits);
     MOCHY_LAUNCHED();
     k_size_bits<<<ceil_div(n_dense, 256), 256, 0, st>>>(n_dense, W, ctx->dense_row, ctx->eoff,
                                                          ctx->theta, ctx->sbits, ctx->dsize);
     MOCHY_LAUNCHED();
   }
-  // heavy nodes
+  // heavy nodes (numbered in node order, so each unit's are one range)
   k_heavy_flags<<<ceil_div(N + 1, 8), 256, 0, st>>>(N, ctx->voff, ctx->vedge, ctx->dense_idx,
                                                     ctx->heavy_thr, flag2);
   MOCHY_LAUNCHED();
   MOCHY_TRY(scan_exclusive_i64(ctx, flag2, pos2, N + 1));
-  int64_t n_heavy = 0;
-  MOCHY_CUDA(cudaMemcpyAsync(&n_heavy, pos2 + N, 8, cudaMemcpyDeviceToHost, st));
+  std::vector<int64_t> hhb((size_t)U + 1, 0);
+  if (U > 1) {
+    // heavy index at each unit's first node (pos is free again; U <= N)
+    k_gather_at<<<ceil_div(U + 1, 256), 256, 0, st>>>(U + 1, pos2, ctx->d_nseg, pos);
+    MOCHY_LAUNCHED();
+    MOCHY_CUDA(cudaMemcpyAsync(hhb.data(), pos, (size_t)(U + 1) * 8, cudaMemcpyDeviceToHost, st));
+  } else {
+    MOCHY_CUDA(cudaMemcpyAsync(&hhb[1], pos2 + N, 8, cudaMemcpyDeviceToHost, st));
+  }
   MOCHY_CUDA(cudaStreamSynchronize(st));
+  const int64_t n_heavy = hhb[U];
   if (N > 0) {
     k_heavy_index<<<ceil_div(N, 256), 256, 0, st>>>(N, flag2, pos2, ctx->heavy_idx);
     MOCHY_LAUNCHED();
   }
+  int64_t hwords = 0;
+  for (int u = 0; u < U; ++u) {
+    seg[u].hbase = hhb[u];
+    seg[u].nboff = hwords;
+    hwords += (hhb[u + 1] - hhb[u]) * seg[u].wn;
+  }
+  MOCHY_CUDA(cudaMemcpyAsync(ctx->d_seg, seg.data(), (size_t)U * sizeof(SegInfo),
+                             cudaMemcpyHostToDevice, st));
   void* nb = nullptr;
-  const size_t b_nbits = (size_t)std::max<int64_t>(n_heavy, 1) * W * 4;
+  const size_t b_nbits = (size_t)std::max<int64_t>(hwords, 1) * 4;
   int rc = dev_alloc(ctx, &nb, b_nbits);
   if (rc < 0) {
     release_split(ctx);
@@ -1172,8 +1367,9 @@ int prepare_split(mochy_ctx* ctx) {
   ctx->nbits_bytes = b_nbits;
   MOCHY_CUDA(cudaMemsetAsync(nb, 0, b_nbits, st));
   if (n_heavy > 0) {
-    k_heavy_bits<<<ceil_div(N, 8), 256, 0, st>>>(N, W, ctx->voff, ctx->vedge, ctx->dense_idx,
-                                                 ctx->heavy_idx, ctx->nbits);
+    k_heavy_bits<<<ceil_div(N, 8), 256, 0, st>>>(N, ctx->d_seg, ctx->d_nseg, U, ctx->voff,
+                                                 ctx->vedge, ctx->dense_idx, ctx->heavy_idx,
+                                                 ctx->nbits);
     MOCHY_LAUNCHED();
   }
   // dense incidence lists (for the light nodes)
@@ -1187,7 +1383,11 @@ int prepare_split(mochy_ctx* ctx) {
     const size_t b_off = al((size_t)(N + 1) * 8);
     const size_t bytes = b_off + (size_t)std::max<int64_t>(n_dinc, 1) * 4;
     void* q;
-    MOCHY_TRY(dev_alloc(ctx, &q, bytes));
+    rc = dev_alloc(ctx, &q, bytes);
+    if (rc < 0) {
+      release_split(ctx);
+      return rc;
+    }
     ctx->dinc_bytes = bytes;
     ctx->dvoff = (int64_t*)q;
     ctx->dvedge = (int32_t*)((char*)q + b_off);
@@ -1213,6 +1413,7 @@ int prepare_split(mochy_ctx* ctx) {
   ctx->n_sparse = E - n_dense;
   ctx->n_heavy = n_heavy;
   ctx->wwords = W;
+  ctx->wmax = wmax;
   ctx->dense_thr_used = thr;
   ctx->split_ready = true;
   return MOCHY_OK;
@@ -1278,19 +1479,45 @@ struct PhaseTimer {
   }
 };
 
-int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
-  cudaStream_t st = ctx->stream;
+// Launch configuration of the three counting kernels (host-only calls, so
+// that the launches themselves can be captured into a CUDA graph).
+struct SplitPlan {
   SplitArgs g;
-  PhaseTimer timer(ctx);
-  if (timer.stats && !ctx->stats) {
-    void* p;
-    MOCHY_TRY(dev_alloc(ctx, &p, 72 * sizeof(unsigned long long)));
-    ctx->stats = (unsigned long long*)p;
+  unsigned grid_open = 0, grid_sparse = 0, grid_dense = 0;
+  size_t smem_sparse = 0, smem_dense = 0;
+  int max_deg = 1;
+};
+
+template <bool kSeg>
+static int plan_kernels(mochy_ctx* ctx, SplitPlan* p) {
+  if (ctx->n_sparse > 0) {
+    const size_t smem = sparse_smem_bytes(p->max_deg);
+    if (smem + 1024 > ctx->smem_optin)
+      return fail(MOCHY_E_UNSUPPORTED, "sparse rows too long for shared memory");
+    MOCHY_CUDA(cudaFuncSetAttribute(k_sparse_triangles<kSeg>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_triangles<kSeg>,
+                                                             kThreads, smem));
+    p->smem_sparse = smem;
+    p->grid_sparse = (unsigned)std::min<int64_t>((int64_t)ctx->num_sms * std::max(per_sm, 1),
+                                                 ctx->n_sparse);
   }
-  if (timer.stats) MOCHY_CUDA(cudaMemsetAsync(ctx->stats, 0, 72 * sizeof(unsigned long long), st));
-  timer.mark("start");
-  MOCHY_TRY(prepare_split(ctx));
-  timer.mark("prepare");
+  if (ctx->n_dense > 0) {
+    const size_t smem = dense_smem_bytes(ctx->wmax);
+    auto kern = ctx->theta == 1 ? k_dense_triangles<true, kSeg> : k_dense_triangles<false, kSeg>;
+    MOCHY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDThreads, smem));
+    p->smem_dense = smem;
+    p->grid_dense = (unsigned)std::min<int64_t>((int64_t)ctx->num_sms * std::max(per_sm, 1),
+                                                ctx->n_dense);
+  }
+  return MOCHY_OK;
+}
+
+static int plan_split(mochy_ctx* ctx, unsigned long long* d_hist, bool stats, SplitPlan* p) {
+  SplitArgs& g = p->g;
   g.n_edges = ctx->n_edges;
   g.eoff = ctx->eoff;
   g.enode = ctx->enode;
@@ -1313,59 +1540,119 @@ int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
   g.dvedge = ctx->dvedge;
   g.dsize = ctx->dsize;
   g.cbits = ctx->sbits + 4 * ctx->wwords;
-  g.stats = timer.stats ? ctx->stats : nullptr;
+  g.stats = stats ? ctx->stats : nullptr;
+  g.order = nullptr;
+  g.n_order = 0;
+  g.queue = nullptr;
+  g.n_units = ctx->n_units;
+  g.nseg = ctx->d_nseg;
+  g.seg = ctx->d_seg;
+  p->grid_open = (unsigned)std::min<int64_t>(ceil_div(ctx->n_edges, kOpenWarps),
+                                             (int64_t)ctx->num_sms * 8);
+  p->max_deg = std::max(1, (int)std::min<int64_t>(ctx->max_deg, ctx->dense_thr_used - 1));
+  return ctx->n_units > 1 ? plan_kernels<true>(ctx, p) : plan_kernels<false>(ctx, p);
+}
+
+// The counting kernels: open pairs, triangles from sparse rows, triangles of
+// dense rows.  Stream operations only (capturable).
+template <bool kSeg>
+static int launch_split(mochy_ctx* ctx, SplitPlan p, PhaseTimer* timer) {
+  cudaStream_t st = ctx->stream;
+  SplitArgs g = p.g;
   MOCHY_CUDA(cudaMemsetAsync(ctx->counters, 0, 16 * sizeof(int32_t), st));
-  // open pairs
-  {
-    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(ctx->n_edges, kOpenWarps),
-                                                      (int64_t)ctx->num_sms * 8);
-    g.order = nullptr;
-    g.n_order = 0;
-    g.queue = nullptr;
-    if (grid > 0) {
-      k_open_pairs<<<grid, kOpenThreads, 0, st>>>(g);
-      MOCHY_LAUNCHED();
-    }
-    timer.mark("open pairs");
+  if (p.grid_open > 0) {
+    k_open_pairs<kSeg><<<p.grid_open, kOpenThreads, 0, st>>>(g);
+    MOCHY_LAUNCHED();
   }
-  // triangles from sparse rows
-  if (ctx->n_sparse > 0) {
-    const int max_deg = (int)std::min<int64_t>(ctx->max_deg, ctx->dense_thr_used - 1);
-    const size_t smem = sparse_smem_bytes(std::max(max_deg, 1));
-    if (smem + 1024 > ctx->smem_optin)
-      return fail(MOCHY_E_UNSUPPORTED, "sparse rows too long for shared memory");
-    MOCHY_CUDA(cudaFuncSetAttribute(k_sparse_triangles,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_triangles,
-                                                             kThreads, smem));
+  if (timer) timer->mark("open pairs");
+  if (p.grid_sparse > 0) {
     g.order = ctx->sparse_order;
     g.n_order = ctx->n_sparse;
     g.queue = ctx->counters + 5;
-    const unsigned grid = (unsigned)std::min<int64_t>((int64_t)ctx->num_sms * std::max(per_sm, 1),
-                                                      ctx->n_sparse);
-    k_sparse_triangles<<<grid, kThreads, smem, st>>>(g, std::max(max_deg, 1));
+    k_sparse_triangles<kSeg><<<p.grid_sparse, kThreads, p.smem_sparse, st>>>(g, p.max_deg);
     MOCHY_LAUNCHED();
-    timer.mark("sparse triangles");
+    if (timer) timer->mark("sparse triangles");
   }
-  // triangles of dense rows
-  if (ctx->n_dense > 0) {
-    const size_t smem = dense_smem_bytes(ctx->wwords);
-    auto kern = ctx->theta == 1 ? k_dense_triangles<true> : k_dense_triangles<false>;
-    MOCHY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDThreads, smem));
+  if (p.grid_dense > 0) {
     g.order = ctx->dense_order;
     g.n_order = ctx->n_dense;
     g.queue = ctx->counters + 6;
-    const unsigned grid = (unsigned)std::min<int64_t>((int64_t)ctx->num_sms * std::max(per_sm, 1),
-                                                      ctx->n_dense);
-    kern<<<grid, kDThreads, smem, st>>>(g);
+    auto kern = ctx->theta == 1 ? k_dense_triangles<true, kSeg> : k_dense_triangles<false, kSeg>;
+    kern<<<p.grid_dense, kDThreads, p.smem_dense, st>>>(g);
     MOCHY_LAUNCHED();
-    timer.mark("dense triangles");
+    if (timer) timer->mark("dense triangles");
+  }
+  return MOCHY_OK;
+}
+
+int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
+  cudaStream_t st = ctx->stream;
+  PhaseTimer timer(ctx);
+  if (timer.stats && !ctx->stats) {
+    void* p;
+    MOCHY_TRY(dev_alloc(ctx, &p, 72 * sizeof(unsigned long long)));
+    ctx->stats = (unsigned long long*)p;
+  }
+  if (timer.stats) MOCHY_CUDA(cudaMemsetAsync(ctx->stats, 0, 72 * sizeof(unsigned long long), st));
+  timer.mark("start");
+  MOCHY_TRY(prepare_split(ctx));
+  timer.mark("prepare");
+  SplitPlan plan;
+  MOCHY_TRY(plan_split(ctx, d_hist, timer.stats, &plan));
+  if (ctx->n_units > 1) {
+    MOCHY_TRY(launch_split<true>(ctx, plan, &timer));
+  } else {
+    MOCHY_TRY(launch_split<false>(ctx, plan, &timer));
   }
   timer.report(ctx);
   return MOCHY_OK;
+}
+
+// The same count with the clearing of the n_units histograms and the three
+// counting kernels captured into one CUDA graph and replayed by a single
+// launch; *ms receives the device time of that launch.  Preparation (which
+// sizes its arrays on the host) runs before the capture.
+int count_split_graph(mochy_ctx* ctx, unsigned long long* d_hist, float* ms) {
+  cudaStream_t st = ctx->stream;
+  MOCHY_TRY(prepare_split(ctx));
+  SplitPlan plan;
+  MOCHY_TRY(plan_split(ctx, d_hist, false, &plan));
+  MOCHY_CUDA(cudaStreamSynchronize(st));
+  MOCHY_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = MOCHY_OK;
+  if (cudaMemsetAsync(d_hist, 0, (size_t)ctx->n_units * 432 * 8, st) != cudaSuccess)
+    rc = fail(MOCHY_E_CUDA, "histogram clear failed during capture");
+  if (rc == MOCHY_OK)
+    rc = ctx->n_units > 1 ? launch_split<true>(ctx, plan, nullptr)
+                          : launch_split<false>(ctx, plan, nullptr);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+  if (rc == MOCHY_OK && ec != cudaSuccess)
+    rc = cuda_fail(ec, "cudaStreamEndCapture", __FILE__, __LINE__);
+  cudaGraphExec_t exec = nullptr;
+  if (rc == MOCHY_OK) {
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    if (ei != cudaSuccess) rc = cuda_fail(ei, "cudaGraphInstantiate", __FILE__, __LINE__);
+  }
+  if (rc == MOCHY_OK) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    const cudaError_t el = cudaGraphLaunch(exec, st);
+    if (el != cudaSuccess) rc = cuda_fail(el, "cudaGraphLaunch", __FILE__, __LINE__);
+    cudaEventRecord(e1, st);
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (rc == MOCHY_OK && es != cudaSuccess) rc = cuda_fail(es, "batch count", __FILE__, __LINE__);
+    float t = 0.f;
+    if (rc == MOCHY_OK) cudaEventElapsedTime(&t, e0, e1);
+    if (ms) *ms = t;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  return rc;
 }
 
 }  // namespace mochy

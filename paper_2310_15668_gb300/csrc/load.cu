@@ -123,12 +123,6 @@ __global__ void k_incidence_pairs(const int64_t* __restrict__ eoff, const int32_
 
 __global__ void k_set_last(int64_t* a, int64_t idx, int64_t v) { a[idx] = v; }
 
-int bits_for(int64_t n) {
-  int b = 1;
-  while (b < 62 && ((int64_t)1 << b) < n) ++b;
-  return b;
-}
-
 }  // namespace
 
 int load_graph(mochy_ctx* ctx, int64_t n_nodes, int64_t n_edges, const int64_t* d_off,

@@ -75,28 +75,20 @@ __global__ void k_offsets(int64_t n_edges, const int64_t* __restrict__ size,
   off[rank[j]] = start[j];
 }
 
-int bits_for(int64_t n) {
-  int b = 1;
-  while (b < 62 && ((int64_t)1 << b) < n) ++b;
-  return b;
-}
-
 }  // namespace
 
-int randomize_graph(mochy_ctx* src, uint64_t seed, uint32_t copy, mochy_ctx* dst) {
-  const int64_t T = src->n_inc, E = src->n_edges, N = src->n_nodes;
-  cudaStream_t st = src->stream;
-  if (T == 0) {
-    return load_graph(dst, N, 0, nullptr, nullptr, nullptr);
-  }
-  // The copy is built in the source context's scratch and loaded into dst.
-  const size_t need = (size_t)T * 28 + (size_t)(E + 1) * 40 + 16 * 256;
+// The transform of Algorithm "transform" on (node, hyperedge) pairs: every
+// hyperedge becomes the set of its nodes, empty hyperedges are dropped, and
+// the result is loaded into dst (which drops repeated hyperedges).  The pairs
+// are sorted in place; temporaries come from work's scratch.
+int pairs_to_hypergraph(mochy_ctx* work, uint32_t* node, uint32_t* edge, int64_t T, int64_t N,
+                        int64_t E, mochy_ctx* dst) {
+  cudaStream_t st = work->stream;
+  const size_t need = (size_t)T * 20 + (size_t)(E + 1) * 40 + 16 * 256;
   void* base;
-  MOCHY_TRY(scratch(src, 0, need, &base));
+  MOCHY_TRY(scratch(work, 0, need, &base));
   char* cur = (char*)base;
   auto carve = [&](size_t b) { void* r = cur; cur += (b + 255) & ~(size_t)255; return r; };
-  uint32_t* node = (uint32_t*)carve((size_t)T * 4);
-  uint32_t* edge = (uint32_t*)carve((size_t)T * 4);
   int64_t* first = (int64_t*)carve((size_t)T * 8);
   int64_t* pos = (int64_t*)carve((size_t)T * 8 + 8);
   int64_t* size = (int64_t*)carve((size_t)(E + 1) * 8);
@@ -105,23 +97,21 @@ int randomize_graph(mochy_ctx* src, uint64_t seed, uint32_t copy, mochy_ctx* dst
   int64_t* start = (int64_t*)carve((size_t)(E + 1) * 8);
   int32_t* nodes_out = (int32_t*)carve((size_t)T * 4);
   const int B = 256;
-  k_chung_lu<<<ceil_div(T, B), B, 0, st>>>(T, src->voff, N, src->eoff, E, seed, copy, node, edge);
-  MOCHY_LAUNCHED();
   // sort by (edge, node): stable by node, then stable by edge
-  MOCHY_TRY(radix_sort_pairs_u32(src, node, edge, T, bits_for(N)));
-  MOCHY_TRY(radix_sort_pairs_u32(src, edge, node, T, bits_for(E)));
+  MOCHY_TRY(radix_sort_pairs_u32(work, node, edge, T, bits_for(N)));
+  MOCHY_TRY(radix_sort_pairs_u32(work, edge, node, T, bits_for(E)));
   MOCHY_CUDA(cudaMemsetAsync(size, 0, (size_t)(E + 1) * 8, st));
   k_firsts<<<ceil_div(T, B), B, 0, st>>>(T, edge, node, first, size);
   MOCHY_LAUNCHED();
-  MOCHY_TRY(scan_exclusive_i64(src, first, pos, T));
+  MOCHY_TRY(scan_exclusive_i64(work, first, pos, T));
   k_gather_nodes<<<ceil_div(T, B), B, 0, st>>>(T, node, first, pos, nodes_out);
   MOCHY_LAUNCHED();
   // offsets of the non-empty hyperedges, in hyperedge order
-  MOCHY_TRY(scan_exclusive_i64(src, size, start, E + 1));
+  MOCHY_TRY(scan_exclusive_i64(work, size, start, E + 1));
   k_nonempty<<<ceil_div(E + 1, B), B, 0, st>>>(E, size, flag);
   MOCHY_LAUNCHED();
   MOCHY_CUDA(cudaMemsetAsync(flag + E, 0, 8, st));
-  MOCHY_TRY(scan_exclusive_i64(src, flag, rank, E + 1));
+  MOCHY_TRY(scan_exclusive_i64(work, flag, rank, E + 1));
   int64_t kept = 0, n_out = 0;
   MOCHY_CUDA(cudaMemcpyAsync(&kept, rank + E, 8, cudaMemcpyDeviceToHost, st));
   MOCHY_CUDA(cudaMemcpyAsync(&n_out, start + E, 8, cudaMemcpyDeviceToHost, st));
@@ -133,6 +123,23 @@ int randomize_graph(mochy_ctx* src, uint64_t seed, uint32_t copy, mochy_ctx* dst
   // hand the arrays to the destination context's loader (which copies them)
   MOCHY_CUDA(cudaStreamSynchronize(st));
   return load_graph(dst, N, kept, off_out, nodes_out, nullptr);
+}
+
+int randomize_graph(mochy_ctx* src, uint64_t seed, uint32_t copy, mochy_ctx* dst) {
+  const int64_t T = src->n_inc, E = src->n_edges, N = src->n_nodes;
+  cudaStream_t st = src->stream;
+  if (T == 0) {
+    return load_graph(dst, N, 0, nullptr, nullptr, nullptr);
+  }
+  // the draws live in scratch slot 2 (the transform takes slots 0, 1 and 3)
+  void* base;
+  MOCHY_TRY(scratch(src, 2, (size_t)T * 8 + 512, &base));
+  uint32_t* node = (uint32_t*)base;
+  uint32_t* edge = node + ((T + 63) & ~(int64_t)63);
+  const int B = 256;
+  k_chung_lu<<<ceil_div(T, B), B, 0, st>>>(T, src->voff, N, src->eoff, E, seed, copy, node, edge);
+  MOCHY_LAUNCHED();
+  return pairs_to_hypergraph(src, node, edge, T, N, E, dst);
 }
 
 }  // namespace mochy

@@ -161,6 +161,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 
 }  // namespace
 
+// bits needed for keys below n
+int bits_for(int64_t n) {
+  int b = 1;
+  while (b < 62 && ((int64_t)1 << b) < n) ++b;
+  return b;
+}
+
 int scan_exclusive_i64(mochy_ctx* ctx, const int64_t* d_in, int64_t* d_out, int64_t n) {
   if (n <= 0) return MOCHY_OK;
   const int64_t nb = (n + kScanTile - 1) / kScanTile;

@@ -76,7 +76,57 @@ __global__ void __launch_bounds__(256) k_sig_cp(const int64_t* __restrict__ coun
          deg + 1, red);
 }
 
+// A batch: block b finishes histogram b / computes the profile of graph b.
+__global__ void __launch_bounds__(512) k_finish_batch(const unsigned long long* __restrict__ hist,
+                                                      const uint8_t* __restrict__ t2h,
+                                                      int64_t* __restrict__ out_h,
+                                                      int64_t* __restrict__ out_3h,
+                                                      int32_t* __restrict__ bad) {
+  __shared__ unsigned long long h[27];
+  const unsigned long long* hb = hist + (int64_t)blockIdx.x * 432;
+  if (threadIdx.x < 27) h[threadIdx.x] = 0ull;
+  __syncthreads();
+  for (int t = threadIdx.x + 1; t <= MOCHY_N_3H; t += blockDim.x) {
+    out_3h[(int64_t)blockIdx.x * MOCHY_N_3H + t - 1] = (int64_t)hb[t];
+    atomicAdd(&h[t2h[t]], hb[t]);
+  }
+  __syncthreads();
+  if (threadIdx.x < MOCHY_N_H)
+    out_h[(int64_t)blockIdx.x * MOCHY_N_H + threadIdx.x] = (int64_t)h[threadIdx.x + 1];
+  if (threadIdx.x == 0 && hb[0] != 0ull) *bad = 1;
+}
+
+// counts: per graph (1 + R) rows; out: per graph sig_h, cp_h, sig_3h, cp_3h
+__global__ void __launch_bounds__(256) k_sig_cp_batch(const int64_t* __restrict__ counts_h,
+                                                      const int64_t* __restrict__ counts_3h,
+                                                      int R, double eps, double* __restrict__ out,
+                                                      int32_t* __restrict__ deg) {
+  __shared__ double red[1];
+  const int64_t b = blockIdx.x;
+  double* o = out + b * 2 * 457;
+  sig_cp(counts_h + b * (R + 1) * MOCHY_N_H, MOCHY_N_H, R, eps, o, o + MOCHY_N_H, deg + 2 * b, red);
+  sig_cp(counts_3h + b * (R + 1) * MOCHY_N_3H, MOCHY_N_3H, R, eps, o + 2 * MOCHY_N_H,
+         o + 2 * MOCHY_N_H + MOCHY_N_3H, deg + 2 * b + 1, red);
+}
+
 }  // namespace
+
+int finish_counts_batch(mochy_ctx* ctx, const unsigned long long* d_hist, int n_hist,
+                        int64_t* d_out_h, int64_t* d_out_3h, int32_t* d_bad) {
+  k_finish_batch<<<n_hist, 512, 0, ctx->stream>>>(d_hist, ctx->tables.t2h, d_out_h, d_out_3h,
+                                                  d_bad);
+  MOCHY_LAUNCHED();
+  return MOCHY_OK;
+}
+
+int significance_cp_batch(mochy_ctx* ctx, const int64_t* d_counts_h, const int64_t* d_counts_3h,
+                          int n_graphs, int32_t n_random, double eps, double* d_out,
+                          int32_t* d_degenerate) {
+  k_sig_cp_batch<<<n_graphs, 256, 0, ctx->stream>>>(d_counts_h, d_counts_3h, n_random, eps, d_out,
+                                                    d_degenerate);
+  MOCHY_LAUNCHED();
+  return MOCHY_OK;
+}
 
 int finish_counts(mochy_ctx* ctx, const unsigned long long* d_hist, int64_t* d_out_h,
                   int64_t* d_out_3h) {

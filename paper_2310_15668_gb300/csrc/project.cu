@@ -139,6 +139,15 @@ __global__ void k_row_cost(int64_t n_edges, const int64_t* __restrict__ noff,
   }
 }
 
+// unit of each row of an order (rows of a batch)
+__global__ void k_row_units(int64_t n, const uint32_t* __restrict__ row,
+                            const int64_t* __restrict__ eoff, const int32_t* __restrict__ enode,
+                            const int64_t* __restrict__ nseg, int n_units,
+                            uint32_t* __restrict__ unit) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) unit[i] = (uint32_t)seg_of(nseg, n_units, enode[eoff[row[i]]]);
+}
+
 }  // namespace
 
 int project_graph(mochy_ctx* ctx) {
@@ -202,6 +211,14 @@ int project_graph(mochy_ctx* ctx) {
   k_row_cost<<<ceil_div(E, 8), 256, 0, st>>>(E, ctx->noff, ctx->nadj, key, val);
   MOCHY_LAUNCHED();
   MOCHY_TRY(radix_sort_pairs_u32(ctx, key, val, E, 32));
+  if (ctx->n_units > 1) {
+    // a batch: rows grouped by hypergraph (stable), so that a block's
+    // consecutive rows mostly belong to one of them
+    k_row_units<<<ceil_div(E, 256), 256, 0, st>>>(E, val, ctx->eoff, ctx->enode, ctx->d_nseg,
+                                                  ctx->n_units, key);
+    MOCHY_LAUNCHED();
+    MOCHY_TRY(radix_sort_pairs_u32(ctx, key, val, E, bits_for(ctx->n_units)));
+  }
   MOCHY_CUDA(cudaMemcpyAsync(ctx->row_order, val, (size_t)E * 4, cudaMemcpyDeviceToDevice, st));
   int32_t md = 0;
   MOCHY_CUDA(cudaMemcpyAsync(&md, maxdeg, 4, cudaMemcpyDeviceToHost, st));

@@ -33,37 +33,48 @@ int choose_dense_threshold(mochy_ctx* ctx) {
   MOCHY_CUDA(cudaMemcpyAsync(off.data(), ctx->noff, off.size() * 8, cudaMemcpyDeviceToHost,
                              ctx->stream));
   MOCHY_CUDA(cudaStreamSynchronize(ctx->stream));
+  // a batch is a disjoint union: every hypergraph has its own dense index
+  // space, so the words per scan are counted per hypergraph
+  const int U = ctx->n_units;
+  std::vector<int64_t> eseg = U > 1 ? ctx->h_eseg : std::vector<int64_t>{0, E};
   std::vector<int64_t> deg((size_t)E);
-  double S = 0.0;
-  for (int64_t i = 0; i < E; ++i) {
-    deg[i] = off[i + 1] - off[i];
-    S += (double)deg[i];
-  }
+  std::vector<double> S((size_t)U, 0.0);
+  for (int u = 0; u < U; ++u)
+    for (int64_t i = eseg[u]; i < eseg[u + 1]; ++i) {
+      deg[i] = off[i + 1] - off[i];
+      S[u] += (double)deg[i];
+    }
   const double word_weight = 0.1;
   int best = -1;
   double best_cost = 0.0;
   for (int64_t thr = 32; thr <= (int64_t)1 << 20; thr <<= 1) {
-    int64_t nd = 0, max_sparse = 0;
-    double Sd = 0.0, sparse = 0.0;
-    for (int64_t i = 0; i < E; ++i) {
-      if (deg[i] >= thr) {
-        ++nd;
-        Sd += (double)deg[i];
-      } else {
-        sparse += (double)deg[i] * (double)deg[i];
-        max_sparse = std::max(max_sparse, deg[i]);
+    int64_t nd_all = 0, max_sparse = 0, wmax = 1;
+    double cost = 0.0;
+    for (int u = 0; u < U; ++u) {
+      int64_t nd = 0;
+      double Sd = 0.0, sparse = 0.0;
+      for (int64_t i = eseg[u]; i < eseg[u + 1]; ++i) {
+        if (deg[i] >= thr) {
+          ++nd;
+          Sd += (double)deg[i];
+        } else {
+          sparse += (double)deg[i] * (double)deg[i];
+          max_sparse = std::max(max_sparse, deg[i]);
+        }
       }
+      const int64_t W = std::max<int64_t>((nd + 31) / 32, 1);
+      wmax = std::max(wmax, U > 1 ? W + 1 : W);   // a unit's window may straddle a word
+      const double fd = S[u] > 0 ? Sd / S[u] : 0.0;
+      cost += word_weight * 0.5 * Sd * fd * (double)W / 3.0 + sparse;
+      nd_all += nd;
     }
-    const int64_t W = std::max<int64_t>((nd + 31) / 32, 1);
-    if (dense_smem_bytes(W) + 1024 > ctx->smem_optin) continue;
+    if (dense_smem_bytes(wmax) + 1024 > ctx->smem_optin) continue;
     if (sparse_smem_bytes((int)std::max<int64_t>(max_sparse, 1)) + 1024 > ctx->smem_optin) continue;
-    const double fd = S > 0 ? Sd / S : 0.0;
-    const double cost = word_weight * 0.5 * Sd * fd * (double)W / 3.0 + sparse;
     if (best < 0 || cost < best_cost) {
       best = (int)thr;
       best_cost = cost;
     }
-    if (nd == 0) break;   // larger thresholds change nothing
+    if (nd_all == 0) break;   // larger thresholds change nothing
   }
   if (best < 0) return fail(MOCHY_E_UNSUPPORTED, "no dense threshold fits shared memory");
   return best;
