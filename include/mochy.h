@@ -227,6 +227,75 @@ int mochy_profile_batch(const mochy_config* cfg, int32_t n_graphs, const int64_t
                         double* cp_3h, int64_t* counts_h, int64_t* counts_3h,
                         int32_t* degenerate, mochy_batch_info* info);
 
+/* ---- Serving ------------------------------------------------------------
+ * A server answers a stream of requests on one GPU with continuous
+ * batching: n_slots worker threads, each with a context and a CUDA stream of
+ * its own, take queued requests in arrival order as soon as a slot is free
+ * and the request's estimated device memory fits the budget beside the
+ * requests already running (cfg->hbm_budget_bytes, else 70% of the device
+ * memory free at creation), so requests that arrive while others run start
+ * as slots and memory free up and their work overlaps on the device.  A
+ * request runs exactly the calls a direct caller would make (mochy_load,
+ * mochy_project, then mochy_count_exact, mochy_count_sampled or
+ * mochy_profile) on a context of its own: its result is the same alone and
+ * in any mix.  The functions may be called from any host thread. */
+typedef struct mochy_server mochy_server;
+
+#define MOCHY_REQ_EXACT 1    /* exact counts (Algorithm "exact_motif_counting") */
+#define MOCHY_REQ_SAMPLED 2  /* sampled counts (method, samples, seed) */
+#define MOCHY_REQ_PROFILE 3  /* significance and CP (n_random, seed) */
+
+typedef struct {
+  int32_t kind;                 /* MOCHY_REQ_* */
+  int64_t n_nodes, n_edges;     /* the hypergraph, as for mochy_load (host */
+  const int64_t* edge_offsets;  /* arrays, copied at submission) */
+  const int32_t* edge_nodes;
+  int32_t method;               /* sampled: MOCHY_A or MOCHY_A_PLUS */
+  int64_t samples;              /* sampled: number of draws */
+  int32_t n_random;             /* profile: randomized copies */
+  uint64_t seed;                /* sampled and profile */
+} mochy_request;
+
+typedef struct {
+  int32_t status;                   /* MOCHY_OK, MOCHY_W_DEGENERATE_CP or an error */
+  int64_t n_wedges;                 /* hyperwedges of the request's hypergraph */
+  int64_t counts_h[MOCHY_N_H];      /* exact counts; sampled raw counts; profile: */
+  int64_t counts_3h[MOCHY_N_3H];    /*   counts of the input */
+  double est_h[MOCHY_N_H];          /* sampled: estimates */
+  double est_3h[MOCHY_N_3H];
+  double sig_h[MOCHY_N_H], cp_h[MOCHY_N_H];      /* profile */
+  double sig_3h[MOCHY_N_3H], cp_3h[MOCHY_N_3H];
+  double queue_ms, service_ms, latency_ms;       /* host clock, submission to result */
+} mochy_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, rejected, queued, in_flight, peak_in_flight;
+  int64_t budget_bytes, peak_reserved_bytes;
+  double p50_ms, p99_ms, mean_ms, max_ms;   /* latency of completed requests (nearest rank) */
+  double throughput_rps;                    /* completed / (last completion - first submission) */
+} mochy_serving_stats;
+
+/* Start a server with n_slots (1..64) workers and room for max_queue queued
+ * requests. */
+int mochy_server_create(mochy_server** out, const mochy_config* cfg, int32_t n_slots,
+                        int32_t max_queue);
+
+/* Queue a request; *ticket identifies it.  MOCHY_E_NOMEM when its estimated
+ * memory exceeds the whole budget, MOCHY_E_BUSY when the queue is full,
+ * MOCHY_E_INVALID for a malformed request. */
+int mochy_server_submit(mochy_server* s, const mochy_request* req, int64_t* ticket);
+
+/* Result of a ticket: returns 1 and fills *out (once; the ticket is then
+ * forgotten) when done, 0 when not done within wait_ms milliseconds. */
+int mochy_server_poll(mochy_server* s, int64_t ticket, mochy_result* out, int32_t wait_ms);
+
+/* Counters and latency percentiles so far. */
+int mochy_server_stats(mochy_server* s, mochy_serving_stats* st);
+
+/* Stop the workers after the requests they are running; queued requests are
+ * dropped.  NULL is accepted. */
+int mochy_server_destroy(mochy_server* s);
+
 /* Region pattern of motif `id` (kind 2: h-motif, kind 3: 3h-motif): states
  * of regions (1)..(7) of Section 2.2 (0 empty, 1 at most theta nodes, 2 more;
  * h-motifs use 0/1). */

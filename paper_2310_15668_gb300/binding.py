@@ -29,8 +29,10 @@ EXPORTS = [
     "mochy_count_exact_subset", "mochy_count_sampled", "mochy_randomize", "mochy_profile",
     "mochy_motif_pattern", "mochy_stream", "mochy_device_bytes", "mochy_kernel_launches",
     "mochy_strerror", "mochy_last_error", "mochy_trace", "mochy_trace_read",
-    "mochy_count_sampled_noalloc", "mochy_profile_batch",
+    "mochy_count_sampled_noalloc", "mochy_profile_batch", "mochy_server_create",
+    "mochy_server_submit", "mochy_server_poll", "mochy_server_stats", "mochy_server_destroy",
 ]
+MOCHY_REQ_EXACT, MOCHY_REQ_SAMPLED, MOCHY_REQ_PROFILE = 1, 2, 3
 
 
 class MochyError(RuntimeError):
@@ -53,6 +55,41 @@ class mochy_batch_info(ctypes.Structure):
                 ("n_units", ctypes.c_int64), ("max_units_per_wave", ctypes.c_int64),
                 ("n_edges", ctypes.c_int64), ("n_wedges", ctypes.c_int64),
                 ("instances", ctypes.c_int64), ("dense_threshold", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class mochy_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_nodes", ctypes.c_int64), ("n_edges", ctypes.c_int64),
+                ("edge_offsets", ctypes.c_void_p), ("edge_nodes", ctypes.c_void_p),
+                ("method", ctypes.c_int32), ("samples", ctypes.c_int64),
+                ("n_random", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class mochy_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_wedges", ctypes.c_int64),
+                ("counts_h", ctypes.c_int64 * N_H), ("counts_3h", ctypes.c_int64 * N_3H),
+                ("est_h", ctypes.c_double * N_H), ("est_3h", ctypes.c_double * N_3H),
+                ("sig_h", ctypes.c_double * N_H), ("cp_h", ctypes.c_double * N_H),
+                ("sig_3h", ctypes.c_double * N_3H), ("cp_3h", ctypes.c_double * N_3H),
+                ("queue_ms", ctypes.c_double), ("service_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = np.ctypeslib.as_array(v).copy() if isinstance(v, ctypes.Array) else v
+        return d
+
+
+class mochy_serving_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "rejected",
+                                              "queued", "in_flight", "peak_in_flight",
+                                              "budget_bytes", "peak_reserved_bytes")] + \
+               [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "max_ms",
+                                               "throughput_rps")]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -105,6 +142,13 @@ def load_library(path: str = LIB_PATH):
             lib.mochy_profile_batch.argtypes = [ctypes.POINTER(mochy_config), i32, vp, vp, vp, vp,
                                                 i32, vp, vp, vp, vp, vp, vp, vp, vp,
                                                 ctypes.POINTER(mochy_batch_info)]
+            lib.mochy_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(mochy_config),
+                                                i32, i32]
+            lib.mochy_server_submit.argtypes = [vp, ctypes.POINTER(mochy_request),
+                                                ctypes.POINTER(i64)]
+            lib.mochy_server_poll.argtypes = [vp, i64, ctypes.POINTER(mochy_result), i32]
+            lib.mochy_server_stats.argtypes = [vp, ctypes.POINTER(mochy_serving_stats)]
+            lib.mochy_server_destroy.argtypes = [vp]
             _lib = lib
     return _lib
 
@@ -358,3 +402,51 @@ class Context:
     @property
     def stream(self):
         return mochy_stream(self.h)
+
+
+class Server:
+    """A mochy_server: continuous batching of count / sampled / profile
+    requests over n_slots workers (each with its own context and stream)."""
+
+    def __init__(self, n_slots: int = 4, max_queue: int = 1 << 16, budget: int = 0,
+                 device: int = 0, dense_threshold: int = 0):
+        cfg = mochy_config_default()
+        cfg.hbm_budget_bytes, cfg.device, cfg.dense_threshold = budget, device, dense_threshold
+        h = ctypes.c_void_p()
+        _check(load_library().mochy_server_create(ctypes.byref(h), ctypes.byref(cfg), n_slots,
+                                                  max_queue), "mochy_server_create")
+        self.h = h.value
+
+    def submit(self, kind: int, n_nodes: int, offsets, nodes, method: int = MOCHY_A_PLUS,
+               samples: int = 0, n_random: int = 0, seed: int = 0) -> int:
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        nod = np.ascontiguousarray(nodes, dtype=np.int32)
+        req = mochy_request(kind, n_nodes, off.size - 1, off.ctypes.data,
+                            nod.ctypes.data if nod.size else None, method, samples, n_random,
+                            seed)
+        t = ctypes.c_int64()
+        _check(load_library().mochy_server_submit(self.h, ctypes.byref(req), ctypes.byref(t)),
+               "mochy_server_submit")
+        return t.value
+
+    def poll(self, ticket: int, wait_ms: int = 0):
+        res = mochy_result()
+        rc = _check(load_library().mochy_server_poll(self.h, ticket, ctypes.byref(res), wait_ms),
+                    "mochy_server_poll")
+        return res.as_dict() if rc == 1 else None
+
+    def stats(self) -> dict:
+        st = mochy_serving_stats()
+        _check(load_library().mochy_server_stats(self.h, ctypes.byref(st)), "mochy_server_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self.h:
+            load_library().mochy_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -72,6 +72,20 @@ int scratch(mochy_ctx* ctx, int slot, size_t bytes, void** p) {
   return MOCHY_OK;
 }
 
+// frees the scratch arena (it grows with the largest call and is kept
+// otherwise)
+void release_scratch(mochy_ctx* ctx) {
+  bool any = false;
+  for (auto& b : ctx->scratch) any = any || b.p;
+  if (!any) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& b : ctx->scratch) {
+    if (b.p) dev_free(ctx, b.p, b.bytes);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+}
+
 static size_t graph_bytes(const mochy_ctx* c, int which) {
   switch (which) {
     case 0: return sizeof(int64_t) * (size_t)(c->n_edges + 1);

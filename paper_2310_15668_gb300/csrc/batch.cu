@@ -347,6 +347,24 @@ int run_wave(const mochy_config& cfg, const Inputs& in, int g0, int g1, int R, O
 }
 
 }  // namespace
+
+// Upper estimate of the device memory one hypergraph needs while it is
+// counted: its line graph has at most sum_v C(d_v, 2) hyperwedges (16 bytes
+// each), plus per-hyperedge, per-incidence and per-node arrays.
+int64_t estimate_graph_bytes(int64_t n_nodes, int64_t n_edges, const int64_t* off,
+                             const int32_t* nodes) {
+  std::vector<int64_t> deg((size_t)std::max<int64_t>(n_nodes, 0), 0);
+  const int64_t T = n_edges > 0 ? off[n_edges] : 0;
+  for (int64_t q = 0; q < T; ++q) {
+    const int32_t v = nodes[q];
+    if (v >= 0 && v < n_nodes) ++deg[(size_t)v];
+  }
+  double w = 0.0;
+  for (int64_t d : deg) w += 0.5 * (double)d * (double)(d - 1);
+  return (int64_t)(16.0 * w + 96.0 * (double)n_edges + 48.0 * (double)T +
+                   16.0 * (double)n_nodes) + (1 << 20);
+}
+
 }  // namespace mochy
 
 using namespace mochy;
@@ -374,10 +392,9 @@ extern "C" int mochy_profile_batch(const mochy_config* cfg_in, int32_t n_graphs,
       return fail(MOCHY_E_INVALID, "null array");
   }
   if (info) memset(info, 0, sizeof(*info));
-  // waves: inputs in order, as many per wave as the memory estimate allows.
-  // A copy's line graph holds at most sum_v C(d_v, 2) hyperwedges (16 bytes
-  // each); the budget is the configured one, else 70% of the device memory
-  // free now.
+  // waves: inputs in order, as many per wave as the memory estimate allows
+  // (estimate_graph_bytes per hypergraph and copy); the budget is the
+  // configured one, else 70% of the device memory free now.
   int64_t budget = cfg.hbm_budget_bytes;
   if (budget <= 0) {
     size_t fr = 0, tot = 0;
@@ -388,18 +405,9 @@ extern "C" int mochy_profile_batch(const mochy_config* cfg_in, int32_t n_graphs,
     budget = (int64_t)((double)fr * 0.7);
   }
   std::vector<int64_t> est((size_t)n_graphs);
-  for (int32_t g = 0; g < n_graphs; ++g) {
-    std::vector<int64_t> deg((size_t)n_nodes[g], 0);
-    const int64_t T = n_edges[g] > 0 ? edge_offsets[g][n_edges[g]] : 0;
-    for (int64_t q = 0; q < T; ++q) {
-      const int32_t v = edge_nodes[g][q];
-      if (v >= 0 && v < n_nodes[g]) ++deg[(size_t)v];
-    }
-    double w = 0.0;
-    for (int64_t d : deg) w += 0.5 * (double)d * (double)(d - 1);
-    est[g] = (int64_t)((double)(n_random + 1) * (16.0 * w + 96.0 * (double)n_edges[g] +
-                                                 48.0 * (double)T + 16.0 * (double)n_nodes[g]));
-  }
+  for (int32_t g = 0; g < n_graphs; ++g)
+    est[g] = (int64_t)(n_random + 1) *
+             estimate_graph_bytes(n_nodes[g], n_edges[g], edge_offsets[g], edge_nodes[g]);
   // MOCHY_BATCH_MAX_GRAPHS caps the inputs per wave (smaller unions)
   int32_t cap = n_graphs;
   if (const char* e = getenv("MOCHY_BATCH_MAX_GRAPHS")) {
