@@ -17,6 +17,18 @@ device-to-host read of the counts.  roofline: the dominant kernel's duration
 is taken live from the library's traced CUDA events.  cpu_baseline: the
 single-threaded CPU oracle on a seeded anchor sample of the same hypergraph.
 
+batch (rank 0, one GPU): significance and CP of 16 seeded hypergraphs (E
+log-uniform in [2,000, 20,000], N = E/2, power-law sizes on [2, 25], Zipf(1.0)
+members), each against 32 randomized copies: CPs/s of mochy_profile_batch
+(all 528 hypergraphs generated on the device and counted in one CUDA-graph
+launch) beside CPs/s of mochy_profile called once per hypergraph, with the
+check that both give identical counts and CPs.
+
+serving (rank 0, one GPU): a Poisson stream of count and CP requests
+(E log-uniform in [1,000, 20,000] from a pool of seeded hypergraphs; 80%
+exact counts, 20% profiles with 4 copies) offered to a mochy_server with
+8 slots and a 120 GB budget; p50/p99 latency and completed requests/s.
+
 Multi-GPU (torchrun): every rank counts its own independently seeded
 hypergraph of the same shape (weak scaling, no collective on the data path).
 `--impl reference` times the CPU oracle instead, on rank 0 only.
@@ -184,6 +196,97 @@ def run_reference(args):
     return 0
 
 
+def _batch_measure(args):
+    """CPs/s of the batched profile against one profile call per hypergraph."""
+    from paper_2310_15668_gb300 import binding as B, synth
+    G, R = args.batch_graphs, args.batch_copies
+    gs = []
+    for i in range(G):
+        s = synth.batch_spec(4, i, args.batch_lo, args.batch_hi)
+        off, nodes = synth.generate(s)
+        gs.append((s.n_nodes, off, nodes))
+    seeds = [1000 + g for g in range(G)]
+    B.mochy_profile_batch(gs[:2], 2, seeds[:2])            # warm-up (library, allocator)
+    t = time.perf_counter()
+    res = B.mochy_profile_batch(gs, R, seeds)
+    t_batch = time.perf_counter() - t
+    t = time.perf_counter()
+    same = True
+    for g, (n, off, nodes) in enumerate(gs):
+        with B.Context() as c:
+            c.load(n, off, nodes)
+            one = c.profile(R, seeds[g])
+        same = same and np.array_equal(res[4][g], one["counts_h"]) \
+            and np.array_equal(res[5][g], one["counts_3h"]) \
+            and np.array_equal(res[1][g], one["cp_h"]) and np.array_equal(res[3][g], one["cp_3h"])
+    t_one = time.perf_counter() - t
+    info = res[7]
+    return {"metric": "CPs/s (significance + characteristic profile)",
+            "value": G / t_batch, "one_at_a_time": G / t_one, "speedup": t_one / t_batch,
+            "identical_counts_and_cps": bool(same),
+            "config": {"workload": f"{G} hypergraphs, E log-uniform in [{args.batch_lo}, "
+                                   f"{args.batch_hi}], N = E/2, sizes s^-2.5 on [2,25], Zipf(1.0)"
+                                   f" members, {R} randomized copies each (scaled-down variant of"
+                                   f" E in [50000, 500000])",
+                       "hypergraphs_counted": int(info["n_units"]),
+                       "triples_counted": int(info["instances"]), "waves": int(info["n_waves"])},
+            "batch_s": t_batch, "one_at_a_time_s": t_one,
+            "phases_ms": {k: info[k] for k in ("ms_generate", "ms_project", "ms_prepare",
+                                               "ms_count", "ms_finish")}}
+
+
+def _serving_measure(args):
+    """Latency and throughput of a Poisson request stream on a mochy_server."""
+    import threading
+    from paper_2310_15668_gb300 import binding as B, synth
+    rng = np.random.default_rng(7)
+    pool = []
+    for i in range(args.serving_pool):
+        s = synth.batch_spec(5, i, 1000, args.serving_hi)
+        off, nodes = synth.generate(s)
+        pool.append((s.n_nodes, off, nodes))
+    n = args.serving_requests
+    gaps = rng.exponential(1.0 / args.serving_rate, size=n)
+    kinds = rng.random(n) < 0.8
+    picks = rng.integers(0, len(pool), size=n)
+    tickets = [0] * n
+    with B.Server(n_slots=args.serving_slots, budget=120 << 30) as srv:
+        def client():
+            t0 = time.perf_counter()
+            due = 0.0
+            for i in range(n):
+                due += gaps[i]
+                wait = t0 + due - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+                g = pool[picks[i]]
+                if kinds[i]:
+                    tickets[i] = srv.submit(B.MOCHY_REQ_EXACT, *g)
+                else:
+                    tickets[i] = srv.submit(B.MOCHY_REQ_PROFILE, *g, n_random=4, seed=i)
+        th = threading.Thread(target=client)
+        t_start = time.perf_counter()
+        th.start()
+        th.join()
+        t_offered = time.perf_counter() - t_start
+        ok = 0
+        for t in tickets:
+            r = None
+            while r is None:
+                r = srv.poll(t, wait_ms=1000)
+            ok += r["status"] >= 0
+        st = srv.stats()
+    return {"metric": "request latency p50/p99 (ms) and completed requests/s",
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "requests_per_s": st["throughput_rps"], "offered_per_s": n / t_offered,
+            "completed": int(ok), "requests": n, "peak_in_flight": int(st["peak_in_flight"]),
+            "config": {"workload": f"{n} requests, Poisson {args.serving_rate}/s, E log-uniform "
+                                   f"in [1000, {args.serving_hi}] from {len(pool)} seeded "
+                                   f"hypergraphs (scaled-down variant of [1e3, 1e6]), 80% exact "
+                                   f"counts, 20% profiles with 4 copies",
+                       "slots": args.serving_slots, "budget_bytes": 120 << 30}}
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = _dist()
@@ -286,6 +389,11 @@ def run_gpu(args):
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = _cpu_baseline(off, nodes, spec.n_nodes, args.cpu_seconds)
+    batch = serving = None
+    if ws == 1 and not args.no_extras:
+        ctx.close()                       # free the medium line graph first
+        batch = _batch_measure(args)
+        serving = _serving_measure(args)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
@@ -293,7 +401,8 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (line graph of 30 GB per step)",
                        "parallelism": f"independent hypergraph per rank x{ws}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk.summary(), "phases_ms": avg, "trace": st}
+            "clocks": clk.summary(), "phases_ms": avg, "trace": st,
+            "batch": batch, "serving": serving}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -310,6 +419,16 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving lines")
+    ap.add_argument("--batch-graphs", type=int, default=16)
+    ap.add_argument("--batch-copies", type=int, default=32)
+    ap.add_argument("--batch-lo", type=int, default=2000)
+    ap.add_argument("--batch-hi", type=int, default=20000)
+    ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--serving-hi", type=int, default=20000)
+    ap.add_argument("--serving-pool", type=int, default=64)
+    ap.add_argument("--serving-slots", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
