@@ -266,6 +266,7 @@ typedef struct {
   double sig_h[MOCHY_N_H], cp_h[MOCHY_N_H];      /* profile */
   double sig_3h[MOCHY_N_3H], cp_3h[MOCHY_N_3H];
   double queue_ms, service_ms, latency_ms;       /* host clock, submission to result */
+  char error[128];                  /* message of a failed request, else empty */
 } mochy_result;
 
 typedef struct {

@@ -74,13 +74,16 @@ class mochy_result(ctypes.Structure):
                 ("sig_h", ctypes.c_double * N_H), ("cp_h", ctypes.c_double * N_H),
                 ("sig_3h", ctypes.c_double * N_3H), ("cp_3h", ctypes.c_double * N_3H),
                 ("queue_ms", ctypes.c_double), ("service_ms", ctypes.c_double),
-                ("latency_ms", ctypes.c_double)]
+                ("latency_ms", ctypes.c_double), ("error", ctypes.c_char * 128)]
 
     def as_dict(self) -> dict:
         d = {}
         for name, _ in self._fields_:
             v = getattr(self, name)
-            d[name] = np.ctypeslib.as_array(v).copy() if isinstance(v, ctypes.Array) else v
+            if isinstance(v, bytes):
+                d[name] = v.decode(errors="replace")
+            else:
+                d[name] = np.ctypeslib.as_array(v).copy() if isinstance(v, ctypes.Array) else v
         return d
 
 

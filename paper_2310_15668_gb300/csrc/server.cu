@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <memory>
@@ -112,6 +113,7 @@ void run_request(mochy_ctx* ctx, const Request& r, mochy_result& out) {
     }
   }
   out.status = rc;
+  if (rc < 0) snprintf(out.error, sizeof(out.error), "%s", mochy_last_error());
   // give the memory back before the next request is admitted
   release_graph(ctx);
   release_scratch(ctx);

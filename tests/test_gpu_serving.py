@@ -88,6 +88,8 @@ def test_mix_overlaps_and_matches_alone():
             assert r is not None
             results.append(r)
         st = srv.stats()
+    bad = [(i, r["status"], r["error"]) for i, r in enumerate(results) if r["status"] < 0]
+    assert not bad
     assert st["completed"] == len(reqs) and st["failed"] == 0
     assert st["peak_in_flight"] >= 2
     assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
