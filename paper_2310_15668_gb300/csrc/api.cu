@@ -2,6 +2,7 @@
 // accounting and the entry points.  Every computation runs in the kernels of
 // the other files; this file only moves arguments and results.
 #include <atomic>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -30,6 +31,23 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
 }
 
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// A kernel's dynamic shared-memory limit is one setting per device, shared by
+// every host thread that launches the kernel; lowering it while another
+// thread is about to launch with a larger size would make that launch fail.
+// So the limit is only ever raised, under a lock.
+int ensure_dynamic_smem(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> set;
+  int dev = 0;
+  MOCHY_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = set[{dev, func}];
+  if (bytes <= cur) return MOCHY_OK;
+  MOCHY_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cur = bytes;
+  return MOCHY_OK;
+}
 
 int dev_alloc(mochy_ctx* ctx, void** p, size_t bytes) {
   *p = nullptr;

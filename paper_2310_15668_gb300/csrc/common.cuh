@@ -165,6 +165,10 @@ struct mochy_ctx {
 
 namespace mochy {
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` (never
+// lowers it; safe with several host threads).
+int ensure_dynamic_smem(const void* func, size_t bytes);
+
 // Memory (budget-checked, tracked per context).
 int dev_alloc(mochy_ctx* ctx, void** p, size_t bytes);
 void dev_free(mochy_ctx* ctx, void* p, size_t bytes);

@@ -213,8 +213,7 @@ int count_exact(mochy_ctx* ctx, const int32_t* d_anchors, int64_t n_anchors,
   // leave room for the kernel's static shared memory
   if (smem + 1024 > ctx->smem_optin)
     return fail(MOCHY_E_UNSUPPORTED, "exact counting supports at most 786432 hyperedges");
-  MOCHY_CUDA(cudaFuncSetAttribute(k_exact_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+  MOCHY_TRY(ensure_dynamic_smem((const void*)k_exact_rows, smem));
   int per_sm = 0;
   MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exact_rows, kExactThreads,
                                                            smem));

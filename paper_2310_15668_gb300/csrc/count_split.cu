@@ -286,6 +286,8 @@ constexpr int kCeff = 16;          // effective sizes kept in the table
 constexpr int kCombo = 64;         // (xa, xb, xt) with each count below 4
 
 constexpr int kLight = 512;        // merged light-node entries per hyperwedge
+constexpr int kSlots = 8;          // per-warp signature slots of popcounted bins (theta = 1)
+constexpr uint32_t kSlotFlush = 1024;   // hyperwedges per slot before it is flushed
 
 struct WarpScratch {
   int64_t lpos[128];     // next unread entry of each light node's dense list
@@ -299,6 +301,13 @@ struct WarpScratch {
   int32_t n[6];          // nA, nB, nT, nlight, pad
   uint32_t table[kCombo * kCeff];
   uint32_t dirty[kCombo * kCeff / 32];
+  // theta = 1: totals of the popcounted bins summed over the row's
+  // hyperwedges that share a signature (their motif codes are equal)
+  uint32_t sacc[kSlots][32];
+  int32_t skey[kSlots];        // signature, -1 when free
+  int32_t srep[kSlots];        // a hyperwedge with that signature: x | B << 8
+  uint32_t sn[kSlots];         // hyperwedges summed since the last flush
+  int32_t snext;               // next slot to evict
 };
 
 // add one bit per lane to a 3-bit sliced counter (c0, c1, c2); a carry out
@@ -415,6 +424,40 @@ __constant__ int c_pop[7][5] = {
     {0, 2, 1, 3, 4}, {1, 1, 1, 3, 4}, {0, 0, 2, 2, 5}};
 constexpr int kPopBins = 28;   // total bins, counted two per register
 
+// Signature of hyperwedge (a, b) for theta = 1: with |e_a| fixed, the motif
+// code of every popcounted bin, and its three "as if open" codes, depend on
+// omega_ab = x and |e_b| = B only through min(x, 4), min(B - x, 5) and
+// min(B, 5) (the bins have xa <= 1, xb <= 2, xt <= 2, so every region
+// involving x or B is either exact or at least 2 beyond these caps).
+__device__ __forceinline__ int pop_signature(int x, int B) {
+  return min(x, 4) + 5 * min(B - x, 5) + 30 * min(B, 5);
+}
+
+// Adds slot `q` of the warp's signature slots to the histogram, as the
+// closed instances of its representative hyperwedge, and frees it.
+template <typename WS>
+__device__ __forceinline__ void flush_slot(WS& me, int q, unsigned long long* hist,
+                                           const uint16_t* lut, int A) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t v = me.sacc[q][lane];
+  if (v && lane < kPopBins) {
+    const int r = me.srep[q];
+    const int x = r & 255, B = r >> 8;
+    int s2 = 0, base = 0;
+    while (base + c_pop[s2][4] <= lane) { base += c_pop[s2][4]; ++s2; }
+    const int xa = c_pop[s2][0], xb = c_pop[s2][1], xt = c_pop[s2][2];
+    const int ce = c_pop[s2][3] + (lane - base);
+    add_triangle(hist, lut, 1, A, B, ce, x, xb + xt, xa + xt, xt, (long long)v);
+  }
+  me.sacc[q][lane] = 0u;
+  __syncwarp();
+  if (lane == 0) {
+    me.skey[q] = -1;
+    me.sn[q] = 0u;
+  }
+  __syncwarp();
+}
+
 template <bool kTheta1, bool kSeg>
 __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -433,6 +476,13 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
   load_lut(lut, g.lut3, hist);
   for (int q = lane; q < kCombo * kCeff; q += 32) me.table[q] = 0u;
   me.dirty[lane] = 0u;
+  for (int q = 0; q < kSlots; ++q) me.sacc[q][lane] = 0u;
+  if (lane < kSlots) {
+    me.skey[lane] = -1;
+    me.sn[lane] = 0u;
+  }
+  if (lane == 0) me.snext = 0;
+  __syncwarp();
   const int theta = g.theta;
   const uint32_t* P0 = g.sbits;
   const uint32_t* P1 = g.sbits + W;
@@ -781,13 +831,36 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           if (lane == 2 * c) mine = lo;
           if (lane == 2 * c + 1) mine = hi2;
         }
-        if (mine && lane < kPopBins) {
-          int s2 = 0, base = 0;
-          while (base + c_pop[s2][4] <= lane) { base += c_pop[s2][4]; ++s2; }
-          const int xa = c_pop[s2][0], xb = c_pop[s2][1], xt = c_pop[s2][2];
-          const int ce = c_pop[s2][3] + (lane - base);
-          add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, (long long)mine);
+        // into the slot of this hyperwedge's signature (found, free, or
+        // evicted round-robin)
+        const int key = pop_signature(x, B);
+        const int sk = lane < kSlots ? me.skey[lane] : -2;
+        const unsigned hit = __ballot_sync(0xffffffffu, sk == key);
+        int q;
+        if (hit) {
+          q = __ffs(hit) - 1;
+        } else {
+          const unsigned fr = __ballot_sync(0xffffffffu, sk == -1);
+          if (fr) {
+            q = __ffs(fr) - 1;
+          } else {
+            q = me.snext;
+            __syncwarp();
+            if (lane == 0) me.snext = (q + 1) % kSlots;
+            flush_slot(me, q, hist, lut, A);
+          }
+          if (lane == 0) {
+            me.skey[q] = key;
+            me.srep[q] = x | (B << 8);
+          }
         }
+        if (lane < kPopBins) me.sacc[q][lane] += mine;
+        __syncwarp();
+        const uint32_t nq = me.sn[q] + 1u;
+        __syncwarp();
+        if (lane == 0) me.sn[q] = nq;
+        __syncwarp();
+        if (nq >= kSlotFlush) flush_slot(me, q, hist, lut, A);
       } else {
 #pragma unroll
         for (int c = 0; c < 2 * kClasses; ++c) {
@@ -821,6 +894,12 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         atomicAdd(&g.stats[7], (unsigned long long)(t_end - t_words1));
       }
       __syncwarp();
+    }
+    // the row is done for this warp: its signature slots go to the histogram
+    // (their codes depend on |e_a|)
+    if (kTheta1) {
+      for (int q = 0; q < kSlots; ++q)
+        if (me.skey[q] >= 0) flush_slot(me, q, hist, lut, A);
     }
   }
   __syncthreads();
@@ -1494,8 +1573,7 @@ static int plan_kernels(mochy_ctx* ctx, SplitPlan* p) {
     const size_t smem = sparse_smem_bytes(p->max_deg);
     if (smem + 1024 > ctx->smem_optin)
       return fail(MOCHY_E_UNSUPPORTED, "sparse rows too long for shared memory");
-    MOCHY_CUDA(cudaFuncSetAttribute(k_sparse_triangles<kSeg>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MOCHY_TRY(ensure_dynamic_smem((const void*)k_sparse_triangles<kSeg>, smem));
     int per_sm = 0;
     MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sparse_triangles<kSeg>,
                                                              kThreads, smem));
@@ -1506,7 +1584,7 @@ static int plan_kernels(mochy_ctx* ctx, SplitPlan* p) {
   if (ctx->n_dense > 0) {
     const size_t smem = dense_smem_bytes(ctx->wmax);
     auto kern = ctx->theta == 1 ? k_dense_triangles<true, kSeg> : k_dense_triangles<false, kSeg>;
-    MOCHY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MOCHY_TRY(ensure_dynamic_smem((const void*)kern, smem));
     int per_sm = 0;
     MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDThreads, smem));
     p->smem_dense = smem;
