@@ -541,16 +541,19 @@ int mochy_trace_read(mochy_ctx* ctx, char* buf, int64_t len) {
              ctx->phase_ms[i]);
     js += item;
   }
-  char tail[512];
+  char tail[1024];
+  const unsigned long long* st = ctx->last_stats;
   snprintf(tail, sizeof(tail),
            "}, \"dense_rows\": %lld, \"dense_threshold\": %d, \"dense_words\": %lld, "
            "\"heavy_nodes\": %lld, \"words_scanned\": %llu, \"candidates\": %llu, "
            "\"table_candidates\": %llu, \"exact_candidates\": %llu, \"light_corrections\": %llu, "
-           "\"clk_setup\": %llu, \"clk_words\": %llu, \"clk_finish\": %llu}",
+           "\"clk_setup\": %llu, \"clk_words\": %llu, \"clk_finish\": %llu, "
+           "\"clk_groups\": %llu, \"clk_light\": %llu, \"clk_sort\": %llu, "
+           "\"light_entries\": %llu, \"dense_hyperwedges\": %llu, \"light_nodes\": %llu, "
+           "\"heavy_bitmaps\": %llu}",
            (long long)ctx->n_dense, ctx->dense_thr_used, (long long)ctx->wwords,
-           (long long)ctx->n_heavy, ctx->last_stats[0], ctx->last_stats[1], ctx->last_stats[2],
-           ctx->last_stats[3], ctx->last_stats[4], ctx->last_stats[5], ctx->last_stats[6],
-           ctx->last_stats[7]);
+           (long long)ctx->n_heavy, st[0], st[1], st[2], st[3], st[4], st[5], st[6], st[7], st[8],
+           st[9], st[10], st[11], st[12], st[13], st[14]);
   js += tail;
   if ((int64_t)js.size() + 1 > len) return fail(MOCHY_E_INVALID, "buffer too small");
   memcpy(buf, js.c_str(), js.size() + 1);

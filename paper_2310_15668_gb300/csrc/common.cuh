@@ -160,7 +160,7 @@ struct mochy_ctx {
   char phase_name[8][24];
   double phase_ms[8];
   unsigned long long* stats = nullptr;   // [8] device counters, when tracing
-  unsigned long long last_stats[8];
+  unsigned long long last_stats[16];
 };
 
 namespace mochy {

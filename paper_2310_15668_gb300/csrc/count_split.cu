@@ -39,6 +39,9 @@ constexpr int kOpenThreads = 256;
 constexpr int kOpenWarps = kOpenThreads / 32;
 constexpr int kTable = 256;   // per-warp class table of the open-pair kernel
 constexpr int kClasses = 5;   // size classes of a simple closed candidate
+// tracing counters: [0..7] totals and cycles, [8..71] rest combinations,
+// [72..79] setup sections and sizes
+constexpr int kStatWords = 80;
 
 // Size class of |e_k| for a closed candidate with both overlaps 1: its motif
 // and its three "as if open" terms depend on |e_k| only through the states
@@ -424,13 +427,17 @@ __constant__ int c_pop[7][5] = {
     {0, 2, 1, 3, 4}, {1, 1, 1, 3, 4}, {0, 0, 2, 2, 5}};
 constexpr int kPopBins = 28;   // total bins, counted two per register
 
-// Signature of hyperwedge (a, b) for theta = 1: with |e_a| fixed, the motif
-// code of every popcounted bin, and its three "as if open" codes, depend on
-// omega_ab = x and |e_b| = B only through min(x, 4), min(B - x, 5) and
-// min(B, 5) (the bins have xa <= 1, xb <= 2, xt <= 2, so every region
-// involving x or B is either exact or at least 2 beyond these caps).
-__device__ __forceinline__ int pop_signature(int x, int B) {
-  return min(x, 4) + 5 * min(B - x, 5) + 30 * min(B, 5);
+// Signature of hyperwedge (a, b) for theta = 1: with A = |e_a| fixed, the
+// motif code of every popcounted bin and its three "as if open" codes depend
+// on omega_ab = x and B = |e_b| only through min(x, 4), min(A - x, 4),
+// min(B - x, 5) and min(B, 5).  The bins have xa <= 1, xb <= 2, xt <= 2
+// (so z = xa + xt <= 2 and y = xb + xt <= 3), and the regions that involve x
+// or B are x - xt, A - x - xa, B - x - xb (closed code), A - x - z, B - x
+// and x (centre a), B - x - y, A - x (centre b), B - y (centre k): each is
+// exact below its cap and at least 2 (the top state) at or above it, and so
+// are the validity tests x + z <= A and x + y <= B.
+__device__ __forceinline__ int pop_signature(int A, int x, int B) {
+  return min(x, 4) + 5 * min(A - x, 4) + 25 * min(B - x, 5) + 150 * min(B, 5);
 }
 
 // Adds slot `q` of the warp's signature slots to the histogram, as the
@@ -583,6 +590,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       unsigned long long st_cand = 0, st_table = 0, st_exact = 0;
       const int64_t first = (int64_t)(bd + 1);
       const int64_t fw = first >> 5;
+      const long long t_groups = g.stats ? clock64() : 0;
       // light nodes: their dense lists (fewer than 32 entries each) from
       // `first` on, merged into one ascending list when they fit, else read
       // through one cursor per node
@@ -605,6 +613,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         n_lent += __popc(kb);
       }
       const bool merged = n_lent <= kLight;
+      const long long t_light = g.stats ? clock64() : 0;
       if (merged && n_lent > 1) {
         // bitonic sort of the merged entries (padded to a power of two)
         int np = 2;
@@ -833,7 +842,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         }
         // into the slot of this hyperwedge's signature (found, free, or
         // evicted round-robin)
-        const int key = pop_signature(x, B);
+        const int key = pop_signature(A, x, B);
         const int sk = lane < kSlots ? me.skey[lane] : -2;
         const unsigned hit = __ballot_sync(0xffffffffu, sk == key);
         int q;
@@ -890,6 +899,13 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       if (g.stats && lane == 0) {
         const long long t_end = clock64();
         atomicAdd(&g.stats[5], (unsigned long long)(t_words0 - t_setup0));
+        atomicAdd(&g.stats[72], (unsigned long long)(t_groups - t_setup0));
+        atomicAdd(&g.stats[73], (unsigned long long)(t_light - t_groups));
+        atomicAdd(&g.stats[74], (unsigned long long)(t_words0 - t_light));
+        atomicAdd(&g.stats[75], (unsigned long long)n_lent);
+        atomicAdd(&g.stats[76], 1ull);
+        atomicAdd(&g.stats[77], (unsigned long long)nL);
+        atomicAdd(&g.stats[78], (unsigned long long)(nA + nB + nT));
         atomicAdd(&g.stats[6], (unsigned long long)(t_words1 - t_words0));
         atomicAdd(&g.stats[7], (unsigned long long)(t_end - t_words1));
       }
@@ -1532,7 +1548,11 @@ struct PhaseTimer {
       c->phase_ms[c->n_phases++] = ms;
     }
     if (stats)
-      cudaMemcpy(c->last_stats, c->stats, sizeof(c->last_stats), cudaMemcpyDeviceToHost);
+    {
+      cudaMemcpy(c->last_stats, c->stats, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+      cudaMemcpy(c->last_stats + 8, c->stats + 72, 8 * sizeof(unsigned long long),
+                 cudaMemcpyDeviceToHost);
+    }
     if (stats && print) {
       unsigned long long combo[64];
       cudaMemcpy(combo, c->stats + 8, sizeof(combo), cudaMemcpyDeviceToHost);
@@ -1668,10 +1688,11 @@ int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
   PhaseTimer timer(ctx);
   if (timer.stats && !ctx->stats) {
     void* p;
-    MOCHY_TRY(dev_alloc(ctx, &p, 72 * sizeof(unsigned long long)));
+    MOCHY_TRY(dev_alloc(ctx, &p, kStatWords * sizeof(unsigned long long)));
     ctx->stats = (unsigned long long*)p;
   }
-  if (timer.stats) MOCHY_CUDA(cudaMemsetAsync(ctx->stats, 0, 72 * sizeof(unsigned long long), st));
+  if (timer.stats)
+    MOCHY_CUDA(cudaMemsetAsync(ctx->stats, 0, kStatWords * sizeof(unsigned long long), st));
   timer.mark("start");
   MOCHY_TRY(prepare_split(ctx));
   timer.mark("prepare");
