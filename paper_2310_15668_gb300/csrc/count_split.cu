@@ -269,19 +269,19 @@ __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
 
 // ---------------------------------------------------------------------------
 // Triangles with three dense rows: CTA per dense row a, warp per hyperwedge
-// (a, b).  Every node of e_a | e_b falls in one of three groups: in e_a only
-// (A), in e_b only (B) or in both (T).  For a candidate e_k adjacent to both,
-//   omega_ak = xa + xt,  omega_bk = xb + xt,  |e_a & e_b & e_k| = xt,
-// where xa, xb, xt count the nodes of each group that e_k holds.  For the
-// nodes with a bitmap ("heavy") these counts are kept bit-sliced, 32
-// candidates per word (2 bits each plus an overflow flag).  The two usual
-// cases, (xa, xb, xt) = (0, 0, 1) and (1, 1, 0), are counted by popcount per
-// size class; any other case goes to a per-warp table keyed by (xa, xb, xt,
-// effective size); a candidate whose counts overflow is classified from its
-// node list.  Candidates that hold a node without bitmap ("light") are
-// corrected afterwards from the short dense incidence lists of those nodes:
-// the class the word loop gave them is taken out and the exact one put in.
-// Shared layout: hist | lut | anodes[64] | WarpScratch[kDWarps] | A1[W]
+// (a, b).  Every dense row keeps its overlaps with the other dense rows of
+// its hypergraph as three bit-planes over the dense index (omega bit 0,
+// omega bit 1, omega >= 4), 32 candidates per word.  For a candidate e_k
+// adjacent to both e_a and e_b, with xa, xb, xt the numbers of nodes of
+// e_a \ e_b, e_b \ e_a and e_a & e_b that e_k holds,
+//   omega_ak = xa + xt,  omega_bk = xb + xt,
+// so only xt = |e_a & e_b & e_k| is counted in the word loop, bit-sliced
+// (3 bits and an overflow flag) from the bitmaps of the nodes of e_a & e_b
+// ("heavy" nodes) or their short lists of dense hyperedges ("light" ones).
+// The usual combinations (xa, xb, xt) are counted by popcount per size bin;
+// any other goes to a per-warp table keyed by (xa, xb, xt, effective size);
+// a candidate with omega >= 4 or xt >= 8 is classified from node lists.
+// Shared layout: hist | lut | anodes[64] | WarpScratch[kDWarps]
 // ---------------------------------------------------------------------------
 constexpr int kDThreads = 256;
 constexpr int kDWarps = kDThreads / 32;
@@ -472,7 +472,6 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
   uint16_t* lut = (uint16_t*)(hist + 432);
   int32_t* anodes = (int32_t*)(lut + 2192);
   WarpScratch* ws = (WarpScratch*)(anodes + 64);
-  uint32_t* A1 = (uint32_t*)(ws + kDWarps);
   const int64_t W = g.wwords;
   __shared__ int64_t slot_s;
   __shared__ int64_t row_next;
@@ -505,7 +504,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
     const int64_t slot = slot_s;
     if (slot >= g.n_order) break;
     // the window of dense words of this row's hypergraph (all of them when
-    // there is one); bitmaps are indexed by word - WLO
+    // there is one); omega planes are indexed by word - WLO
     int64_t WLO = 0, WHI = W, WN = W, hbase = 0, dboff = 0, dbase = 0;
     const uint32_t* NB = g.nbits;
     if (kSeg) {
@@ -524,13 +523,8 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
     const int64_t rb = g.noff[a], re = g.noff[a + 1];
     const int A = (int)(g.eoff[a + 1] - g.eoff[a]);
     if (threadIdx.x < A) anodes[threadIdx.x] = g.enode[g.eoff[a] + threadIdx.x];
-    for (int64_t q = threadIdx.x; q < WN; q += kDThreads) A1[q] = 0u;
-    __syncthreads();
-    for (int64_t p = rb + threadIdx.x; p < re; p += kDThreads) {
-      const int kd = g.dense_idx[ent_id(g.nadj[p])];
-      if (kd >= 0) atomicOr(&A1[(kd >> 5) - WLO], 1u << (kd & 31));
-    }
-    __syncthreads();
+    // omega planes of row a (bit 0, bit 1, >= 4), indexed by word - WLO
+    const uint32_t* AR = g.dbits + dboff + (int64_t)(ad - dbase) * 3 * WN;
     if (threadIdx.x == 0) row_next = rb;
     __syncthreads();
     while (true) {
@@ -549,40 +543,28 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       if (lane + 32 < B) me.bnodes[lane + 32] = g.enode[g.eoff[b] + lane + 32];
       if (lane < 5) me.n[lane] = 0;
       __syncwarp();
-      // groups of the nodes of e_a | e_b
-      for (int base = 0; base < A + B; base += 32) {
+      // the nodes of e_a & e_b (group T): with a bitmap ("heavy") or a short
+      // list of dense hyperedges ("light")
+      for (int base = 0; base < A; base += 32) {
         const int l = base + lane;
-        int32_t u = -1;
-        int grp = -1;
-        if (l < A) {
-          u = anodes[l];
-          grp = has_node(me.bnodes, B, u) ? 2 : 0;
-        } else if (l < A + B) {
-          u = me.bnodes[l - A];
-          grp = has_node(anodes, A, u) ? -1 : 1;     // common nodes come from e_a
-        }
-        const int hv = grp >= 0 ? g.heavy_idx[u] : -1;
-        for (int gg = 0; gg < 3; ++gg) {
-          const bool mine = grp == gg && hv >= 0;
-          const unsigned bal = __ballot_sync(0xffffffffu, mine);
-          if (mine) me.hidx[gg][me.n[gg] + __popc(bal & ((1u << lane) - 1u))] = hv - (int)hbase;
-          __syncwarp();
-          if (lane == 0) me.n[gg] += __popc(bal);
-          __syncwarp();
-        }
-        const bool lt = grp >= 0 && hv < 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, lt);
-        if (lt) {
-          const int pos = me.n[3] + __popc(bal & ((1u << lane) - 1u));
-          me.light[pos] = u;
-          me.lgrp[pos] = grp;
-        }
+        const int32_t u = l < A ? anodes[l] : -1;
+        const bool inT = l < A && has_node(me.bnodes, B, u);
+        const int hv = inT ? g.heavy_idx[u] : -1;
+        const bool hvy = inT && hv >= 0, lt = inT && hv < 0;
+        const unsigned bh = __ballot_sync(0xffffffffu, hvy);
+        const unsigned bl = __ballot_sync(0xffffffffu, lt);
+        const int nh0 = me.n[2], nl0 = me.n[3];
+        if (hvy) me.hidx[2][nh0 + __popc(bh & ((1u << lane) - 1u))] = hv - (int)hbase;
+        if (lt) me.light[nl0 + __popc(bl & ((1u << lane) - 1u))] = u;
         __syncwarp();
-        if (lane == 0) me.n[3] += __popc(bal);
+        if (lane == 0) {
+          me.n[2] = nh0 + __popc(bh);
+          me.n[3] = nl0 + __popc(bl);
+        }
         __syncwarp();
       }
-      const int nA = me.n[0], nB = me.n[1], nT = me.n[2], nL = me.n[3];
-      const uint32_t* B1 = g.dbits + dboff + (int64_t)(bd - dbase) * 2 * WN;
+      const int nT = me.n[2], nL = me.n[3];
+      const uint32_t* BR = g.dbits + dboff + (int64_t)(bd - dbase) * 3 * WN;
       // per-lane counters: 14 pairs of 16-bit bins (theta = 1) or 10 bins
       uint32_t cnt[14];
 #pragma unroll
@@ -591,7 +573,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       const int64_t first = (int64_t)(bd + 1);
       const int64_t fw = first >> 5;
       const long long t_groups = g.stats ? clock64() : 0;
-      // light nodes: their dense lists (fewer than 32 entries each) from
+      // light T nodes: their dense lists (fewer than 32 entries each) from
       // `first` on, merged into one ascending list when they fit, else read
       // through one cursor per node
       int n_lent = 0;
@@ -609,7 +591,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         const bool keep = e != 0x7fffffff && e >= first;
         const unsigned kb = __ballot_sync(0xffffffffu, keep);
         if (keep && n_lent + __popc(kb) <= kLight)
-          me.lent[n_lent + __popc(kb & ((1u << lane) - 1u))] = (e << 2) | me.lgrp[l];
+          me.lent[n_lent + __popc(kb & ((1u << lane) - 1u))] = e;
         n_lent += __popc(kb);
       }
       const bool merged = n_lent <= kLight;
@@ -641,32 +623,26 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       for (int64_t w0 = fw; w0 < WHI; w0 += 32) {
         const bool inr = w0 + lane < WHI;
         const int64_t w = inr ? w0 + lane : WHI - 1;
-        uint32_t m = inr ? (A1[w - WLO] & __ldg(&B1[w - WLO])) : 0u;
+        const int64_t wl = w - WLO;
+        // omega_ak and omega_bk of the 32 candidates of word w, as planes
+        const uint32_t qa0 = __ldg(&AR[wl]), qa1 = __ldg(&AR[WN + wl]), qav = __ldg(&AR[2 * WN + wl]);
+        const uint32_t qb0 = __ldg(&BR[wl]), qb1 = __ldg(&BR[WN + wl]), qbv = __ldg(&BR[2 * WN + wl]);
+        uint32_t m = inr ? ((qa0 | qa1 | qav) & (qb0 | qb1 | qbv)) : 0u;
         if (w == fw) m &= 0xffffffffu << (first & 31);
-        uint32_t a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0, t0 = 0, t1 = 0, t2 = 0, ovf = 0;
-        for (int h = 0; h < nA; ++h)
-          slice_add(a0, a1, a2, ovf, __ldg(&NB[(int64_t)me.hidx[0][h] * WN + (w - WLO)]));
-        for (int h = 0; h < nB; ++h)
-          slice_add(b0, b1, b2, ovf, __ldg(&NB[(int64_t)me.hidx[1][h] * WN + (w - WLO)]));
+        // xt = |e_a & e_b & e_k|, bit-sliced (3 bits and an overflow flag)
+        uint32_t t0 = 0, t1 = 0, t2 = 0, ovf = 0;
         for (int h = 0; h < nT; ++h)
-          slice_add(t0, t1, t2, ovf, __ldg(&NB[(int64_t)me.hidx[2][h] * WN + (w - WLO)]));
-        // light nodes with a dense index in this iteration's 32 words
+          slice_add(t0, t1, t2, ovf, __ldg(&NB[(int64_t)me.hidx[2][h] * WN + wl]));
+        // light T nodes with a dense index in this iteration's 32 words
         const int64_t hi64 = (w0 + 32) * 32;
         const int32_t hi = hi64 < 0x7fffffff ? (int32_t)hi64 : 0x7fffffff;
         if (merged) {
           while (lcur < n_lent) {
             const int32_t e = lcur + lane < n_lent ? me.lent[lcur + lane] : 0x7fffffff;
-            const int nin = __popc(__ballot_sync(0xffffffffu, (e >> 2) < hi && e != 0x7fffffff));
+            const int nin = __popc(__ballot_sync(0xffffffffu, e < hi && e != 0x7fffffff));
             for (int j = 0; j < nin; ++j) {
-              const int32_t ej = __shfl_sync(0xffffffffu, e, j);
-              const int32_t kd = ej >> 2;
-              if ((int64_t)(kd >> 5) == w && inr) {
-                const uint32_t bitm = 1u << (kd & 31);
-                const int grp = ej & 3;
-                if (grp == 0) slice_add(a0, a1, a2, ovf, bitm);
-                else if (grp == 1) slice_add(b0, b1, b2, ovf, bitm);
-                else slice_add(t0, t1, t2, ovf, bitm);
-              }
+              const int32_t kd = __shfl_sync(0xffffffffu, e, j);
+              if ((int64_t)(kd >> 5) == w && inr) slice_add(t0, t1, t2, ovf, 1u << (kd & 31));
             }
             lcur += nin;
             if (nin < 32) break;
@@ -677,15 +653,9 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
             const int64_t pos = me.lpos[l], le = me.lend[l];
             const int32_t e = pos + lane < le ? g.dvedge[pos + lane] : 0x7fffffff;
             const int nin = __popc(__ballot_sync(0xffffffffu, e < hi));
-            const int grp = me.lgrp[l];
             for (int j = 0; j < nin; ++j) {
               const int32_t kd = __shfl_sync(0xffffffffu, e, j);
-              if ((int64_t)(kd >> 5) == w && inr) {
-                const uint32_t bitm = 1u << (kd & 31);
-                if (grp == 0) slice_add(a0, a1, a2, ovf, bitm);
-                else if (grp == 1) slice_add(b0, b1, b2, ovf, bitm);
-                else slice_add(t0, t1, t2, ovf, bitm);
-              }
+              if ((int64_t)(kd >> 5) == w && inr) slice_add(t0, t1, t2, ovf, 1u << (kd & 31));
             }
             const int32_t nx = __shfl_sync(0xffffffffu, e, nin & 31);
             __syncwarp();
@@ -696,22 +666,27 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
             __syncwarp();
           }
         }
-        const uint32_t za = a0 | a1 | a2, zb = b0 | b1 | b2, zt = t0 | t1 | t2;
-        ovf &= m;
-        const uint32_t valid = m & (za | zt) & (zb | zt) & ~ovf;
-        const uint32_t one_a = a0 & ~a1 & ~a2, one_b = b0 & ~b1 & ~b2, one_t = t0 & ~t1 & ~t2;
-        const uint32_t s001 = valid & ~za & ~zb & one_t;
-        const uint32_t s110 = valid & one_a & one_b & ~zt;
+        // omega >= 4 or xt >= 8: classified from node lists below
+        ovf = (ovf | qav | qbv) & m;
+        const uint32_t valid = m & ~ovf;
+        // on valid bits omega is 1..3: (bit1, bit0) = 01, 10 or 11
+        const uint32_t a1m = qa0 & ~qa1, a2m = ~qa0 & qa1;
+        const uint32_t b1m = qb0 & ~qb1, b2m = ~qb0 & qb1, b3m = qb0 & qb1;
+        const uint32_t zt = t0 | t1 | t2;
+        const uint32_t one_t = t0 & ~t1 & ~t2;
+        // (xa, xb, xt) = (omega_ak - xt, omega_bk - xt, xt)
+        const uint32_t s001 = valid & a1m & b1m & one_t;
+        const uint32_t s110 = valid & a1m & b1m & ~zt;
         uint32_t done = s001 | s110;
         const uint32_t p0 = __ldg(&P0[w]), p1 = __ldg(&P1[w]), p2 = __ldg(&P2[w]), p3 = __ldg(&P3[w]);
         const SizeMasks sz(p0, p1, p2, p3);
         if (kTheta1) {
-          const uint32_t two_b = ~b0 & b1 & ~b2, two_t = ~t0 & t1 & ~t2;
-          const uint32_t s011 = valid & ~za & one_b & one_t;
-          const uint32_t s101 = valid & one_a & ~zb & one_t;
-          const uint32_t s021 = valid & ~za & two_b & one_t;
-          const uint32_t s111 = valid & one_a & one_b & one_t;
-          const uint32_t s002 = valid & ~za & ~zb & two_t;
+          const uint32_t two_t = ~t0 & t1 & ~t2;
+          const uint32_t s011 = valid & a1m & b2m & one_t;
+          const uint32_t s101 = valid & a2m & b1m & one_t;
+          const uint32_t s021 = valid & a1m & b3m & one_t;
+          const uint32_t s111 = valid & a2m & b2m & one_t;
+          const uint32_t s002 = valid & a2m & b2m & two_t;
           done |= s011 | s101 | s021 | s111 | s002;
           // bins: (0,0,1) 1,2,3,4+ | (0,1,1) 2,3,4,5+ | (1,0,1) 2,3,4,5+ |
           // (1,1,0) 2,3,4+ | (0,2,1) 3,4,5,6+ | (1,1,1) 3,4,5,6+ | (0,0,2) 2,3,4,5,6+
@@ -744,7 +719,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         }
         // remaining candidates, processed by the whole warp 32 at a time:
         // lane i takes the i-th remaining candidate of the iteration (from any
-        // lane's word), reads that word's counters by shuffle, and equal
+        // lane's word), reads that word's planes by shuffle, and equal
         // (combination, size) keys are added once per group of lanes
         {
           const uint32_t rest = valid & ~done;
@@ -768,10 +743,8 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
             src &= 31;
             const int ex = __shfl_sync(0xffffffffu, incl - rc, src);
             const uint32_t rs = __shfl_sync(0xffffffffu, rest, src);
-            const uint32_t sa0 = __shfl_sync(0xffffffffu, a0, src), sa1 = __shfl_sync(0xffffffffu, a1, src),
-                           sa2 = __shfl_sync(0xffffffffu, a2, src);
-            const uint32_t sb0 = __shfl_sync(0xffffffffu, b0, src), sb1 = __shfl_sync(0xffffffffu, b1, src),
-                           sb2 = __shfl_sync(0xffffffffu, b2, src);
+            const uint32_t sa0 = __shfl_sync(0xffffffffu, qa0, src), sa1 = __shfl_sync(0xffffffffu, qa1, src);
+            const uint32_t sb0 = __shfl_sync(0xffffffffu, qb0, src), sb1 = __shfl_sync(0xffffffffu, qb1, src);
             const uint32_t st0 = __shfl_sync(0xffffffffu, t0, src), st1 = __shfl_sync(0xffffffffu, t1, src),
                            st2 = __shfl_sync(0xffffffffu, t2, src);
             const uint32_t sp0 = __shfl_sync(0xffffffffu, p0, src), sp1 = __shfl_sync(0xffffffffu, p1, src),
@@ -782,9 +755,9 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
             int xa = 0, xb = 0, xt = 0, ce = 0;
             if (act) {
               const int bit = __fns(rs, 0, item - ex + 1);
-              xa = sval3(sa0, sa1, sa2, bit);
-              xb = sval3(sb0, sb1, sb2, bit);
               xt = sval3(st0, st1, st2, bit);
+              xa = (int)((sa0 >> bit) & 1u) + 2 * (int)((sa1 >> bit) & 1u) - xt;
+              xb = (int)((sb0 >> bit) & 1u) + 2 * (int)((sb1 >> bit) & 1u) - xt;
               int C = (int)((sp0 >> bit) & 1u) | ((int)((sp1 >> bit) & 1u) << 1) |
                       ((int)((sp2 >> bit) & 1u) << 2) | ((int)((sp3 >> bit) & 1u) << 3);
               if (C >= 15) C = g.dsize[sw * 32 + bit];
@@ -905,7 +878,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         atomicAdd(&g.stats[75], (unsigned long long)n_lent);
         atomicAdd(&g.stats[76], 1ull);
         atomicAdd(&g.stats[77], (unsigned long long)nL);
-        atomicAdd(&g.stats[78], (unsigned long long)(nA + nB + nT));
+        atomicAdd(&g.stats[78], (unsigned long long)nT);
         atomicAdd(&g.stats[6], (unsigned long long)(t_words1 - t_words0));
         atomicAdd(&g.stats[7], (unsigned long long)(t_end - t_words1));
       }
@@ -990,20 +963,20 @@ __global__ void __launch_bounds__(kThreads) k_sparse_triangles(SplitArgs g, int 
       __syncwarp();
       if (bd >= 0) {
         // b dense: every k after b is dense with a larger dense index
-        const uint32_t* B1 = g.dbits + dboff + (int64_t)(bd - dbase) * 2 * WN;
-        const uint32_t* B2 = B1 + WN;
+        // omega planes of row b: omega_bk = bit0 + 2 bit1, or >= 4
+        const uint32_t* Q = g.dbits + dboff + (int64_t)(bd - dbase) * 3 * WN;
         for (int q = lane; q < deg; q += 32) {
           const int kd = sdi[q];
           if (kd <= bd) continue;
           const uint32_t bit = 1u << (kd & 31);
-          if (!(__ldg(&B1[(kd >> 5) - WLO]) & bit)) continue;
+          const int64_t wq = (kd >> 5) - WLO;
+          const uint32_t q0 = __ldg(&Q[wq]) & bit, q1 = __ldg(&Q[WN + wq]) & bit,
+                         qv = __ldg(&Q[2 * WN + wq]) & bit;
+          if (!(q0 | q1 | qv)) continue;
           const int64_t k = skey[q];
           const int C = ssz[q];
-          int y = 1;
-          if (__ldg(&B2[(kd >> 5) - WLO]) & bit) {
-            const int64_t kb = g.eoff[k];
-            y = sorted_overlap(bnodes, B, g.enode + kb, C);
-          }
+          int y = (q0 ? 1 : 0) + (q1 ? 2 : 0);
+          if (qv) y = sorted_overlap(bnodes, B, g.enode + g.eoff[k], C);
           const int z = entry_omega(sw1[q], A);
           int t;
           if (A <= kMaskedMax) {
@@ -1120,14 +1093,20 @@ __global__ void k_dense_bits(int64_t n_dense, const SegInfo* __restrict__ seg,
     const SegInfo sg = seg[seg_of(dbase, n_units, r)];
     const int64_t b = drow[r];
     const int B = (int)(eoff[b + 1] - eoff[b]);
-    uint32_t* B1 = dbits + sg.dboff + (r - sg.dbase) * 2 * sg.wn;
-    uint32_t* B2 = B1 + sg.wn;
+    uint32_t* Q = dbits + sg.dboff + (r - sg.dbase) * 3 * sg.wn;
     for (int64_t p = noff[b] + threadIdx.x; p < noff[b + 1]; p += blockDim.x) {
       const uint2 e = nadj[p];
       const int kd = didx[ent_id(e)];
       if (kd < 0) continue;
-      atomicOr(&B1[(kd >> 5) - sg.wlo], 1u << (kd & 31));
-      if (entry_omega(e.y, B) >= 2) atomicOr(&B2[(kd >> 5) - sg.wlo], 1u << (kd & 31));
+      const int om = entry_omega(e.y, B);
+      const int64_t wq = (kd >> 5) - sg.wlo;
+      const uint32_t bit = 1u << (kd & 31);
+      if (om >= 4) {
+        atomicOr(&Q[2 * sg.wn + wq], bit);
+      } else {
+        if (om & 1) atomicOr(&Q[wq], bit);
+        if (om & 2) atomicOr(&Q[sg.wn + wq], bit);
+      }
     }
   }
 }
@@ -1288,7 +1267,8 @@ void release_split(mochy_ctx* ctx) {
 int choose_dense_threshold(mochy_ctx* ctx);   // tune.cu
 
 size_t dense_smem_bytes(int64_t W) {
-  return 432 * 8 + 2192 * 2 + 64 * 4 + sizeof(WarpScratch) * kDWarps + (size_t)W * 4;
+  (void)W;   // the rows' omega planes are read from global memory
+  return 432 * 8 + 2192 * 2 + 64 * 4 + sizeof(WarpScratch) * kDWarps;
 }
 
 size_t sparse_smem_bytes(int max_deg) {
@@ -1380,7 +1360,7 @@ int prepare_split(mochy_ctx* ctx) {
     sg.wlo = hdb[u] >> 5;
     sg.wn = nd > 0 ? ((hdb[u + 1] + 31) >> 5) - sg.wlo : 0;
     sg.dboff = dwords;
-    dwords += nd * 2 * sg.wn;
+    dwords += nd * 3 * sg.wn;
     sg.hbase = sg.nboff = 0;
     wmax = std::max(wmax, sg.wn);
   }
