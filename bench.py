@@ -126,6 +126,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_over_ranks(ms: float, units: float, world_size: int, device: str):
+    """Whole-job timing over ranks: the slowest rank's time and the work of
+    all ranks (each rank counts its own hypergraph; no data-path exchange)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -335,13 +348,8 @@ def run_gpu(args):
     launches = B.mochy_kernel_launches() - launches0
     ms = start.elapsed_time(end)
     B.mochy_trace(ctx.h, 0)
-    t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    total = torch.tensor([float(instances) * args.steps], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(total)
-    ms_max = float(t_max.item())
-    value = float(total.item()) / (ms_max / 1000.0)
+    ms_max, total_units = reduce_over_ranks(ms, float(instances) * args.steps, ws, "cuda")
+    value = total_units / (ms_max / 1000.0)
 
     # kernel statistics (scanned words) from one more, untimed step at trace level 2
     B.mochy_trace(ctx.h, 2)
@@ -377,11 +385,13 @@ def run_gpu(args):
     st = stats_trace
     roof = None
     if dom == "dense triangles" and avg[dom] > 0:
-        # algorithmic bytes: every scanned word reads one word of the partner
-        # row's bitmap, four size planes, and the words of the bitmaps of the
-        # heavy nodes of e_a | e_b (about two per word on this workload)
+        # algorithmic bytes: every scanned word reads the three overlap planes
+        # of row a and of row b, the four size planes, and one bitmap word per
+        # heavy node of e_a & e_b (their mean number per hyperwedge is traced)
         words = float(st.get("words_scanned", 0))
-        algo = words * 4.0 * (1 + 4 + 2)
+        hw = float(st.get("dense_hyperwedges", 0)) or 1.0
+        n_t = float(st.get("heavy_bitmaps", 0)) / hw
+        algo = words * 4.0 * (3 + 3 + 4 + n_t)
         achieved = algo / (avg[dom] / 1000.0) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "kernel": "k_dense_triangles",
