@@ -25,9 +25,10 @@ launch) beside CPs/s of mochy_profile called once per hypergraph, with the
 check that both give identical counts and CPs.
 
 serving (rank 0, one GPU): a Poisson stream of count and CP requests
-(E log-uniform in [1,000, 20,000] from a pool of seeded hypergraphs; 80%
-exact counts, 20% profiles with 4 copies) offered to a mochy_server with
-8 slots and a 120 GB budget; p50/p99 latency and completed requests/s.
+(E log-uniform in [1,000, 4,000] from a pool of seeded hypergraphs; 90%
+exact counts, 10% profiles with 4 copies) offered at 200/s to a
+mochy_server with 8 slots and a 120 GB budget; p50/p99 latency and
+completed requests/s.
 
 Multi-GPU (torchrun): every rank counts its own independently seeded
 hypergraph of the same shape (weak scaling, no collective on the data path).
@@ -260,7 +261,7 @@ def _serving_measure(args):
         pool.append((s.n_nodes, off, nodes))
     n = args.serving_requests
     gaps = rng.exponential(1.0 / args.serving_rate, size=n)
-    kinds = rng.random(n) < 0.8
+    kinds = rng.random(n) < 1.0 - args.serving_profiles
     picks = rng.integers(0, len(pool), size=n)
     tickets = [0] * n
     with B.Server(n_slots=args.serving_slots, budget=120 << 30) as srv:
@@ -295,8 +296,9 @@ def _serving_measure(args):
             "completed": int(ok), "requests": n, "peak_in_flight": int(st["peak_in_flight"]),
             "config": {"workload": f"{n} requests, Poisson {args.serving_rate}/s, E log-uniform "
                                    f"in [1000, {args.serving_hi}] from {len(pool)} seeded "
-                                   f"hypergraphs (scaled-down variant of [1e3, 1e6]), 80% exact "
-                                   f"counts, 20% profiles with 4 copies",
+                                   f"hypergraphs (scaled-down variant of [1e3, 1e6]), "
+                                   f"{100 * (1 - args.serving_profiles):.0f}% exact counts, "
+                                   f"{100 * args.serving_profiles:.0f}% profiles with 4 copies",
                        "slots": args.serving_slots, "budget_bytes": 120 << 30}}
 
 
@@ -436,7 +438,8 @@ def main():
     ap.add_argument("--batch-hi", type=int, default=20000)
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--serving-rate", type=float, default=200.0)
-    ap.add_argument("--serving-hi", type=int, default=20000)
+    ap.add_argument("--serving-hi", type=int, default=4000)
+    ap.add_argument("--serving-profiles", type=float, default=0.1)
     ap.add_argument("--serving-pool", type=int, default=64)
     ap.add_argument("--serving-slots", type=int, default=8)
     args = ap.parse_args()

@@ -120,7 +120,7 @@ struct mochy_ctx {
   int64_t n_dense = 0, n_sparse = 0, n_heavy = 0, wwords = 0;
   int32_t* dense_idx = nullptr;   // [E]  dense index or -1
   int32_t* dense_row = nullptr;   // [n_dense]
-  uint32_t* dbits = nullptr;      // per dense row 3 planes over its window: omega bit 0, bit 1, >= 4
+  uint32_t* dbits = nullptr;      // per dense row 3 planes over its window: bits of min(omega, 7)
   int32_t* heavy_idx = nullptr;   // [N]  heavy index or -1
   uint32_t* nbits = nullptr;      // [n_heavy][wwords]  dense members of E_v
   uint32_t* sbits = nullptr;      // [5][wwords]  size class of dense rows

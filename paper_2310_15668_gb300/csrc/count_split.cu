@@ -270,8 +270,8 @@ __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
 // ---------------------------------------------------------------------------
 // Triangles with three dense rows: CTA per dense row a, warp per hyperwedge
 // (a, b).  Every dense row keeps its overlaps with the other dense rows of
-// its hypergraph as three bit-planes over the dense index (omega bit 0,
-// omega bit 1, omega >= 4), 32 candidates per word.  For a candidate e_k
+// its hypergraph as three bit-planes over the dense index (bits 0, 1, 2 of
+// min(omega, 7)), 32 candidates per word.  For a candidate e_k
 // adjacent to both e_a and e_b, with xa, xb, xt the numbers of nodes of
 // e_a \ e_b, e_b \ e_a and e_a & e_b that e_k holds,
 //   omega_ak = xa + xt,  omega_bk = xb + xt,
@@ -280,7 +280,8 @@ __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
 // ("heavy" nodes) or their short lists of dense hyperedges ("light" ones).
 // The usual combinations (xa, xb, xt) are counted by popcount per size bin;
 // any other goes to a per-warp table keyed by (xa, xb, xt, effective size);
-// a candidate with omega >= 4 or xt >= 8 is classified from node lists.
+// a candidate with an omega of 7 or more, or xt >= 8, is classified from
+// node lists.
 // Shared layout: hist | lut | anodes[64] | WarpScratch[kDWarps]
 // ---------------------------------------------------------------------------
 constexpr int kDThreads = 256;
@@ -523,7 +524,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
     const int64_t rb = g.noff[a], re = g.noff[a + 1];
     const int A = (int)(g.eoff[a + 1] - g.eoff[a]);
     if (threadIdx.x < A) anodes[threadIdx.x] = g.enode[g.eoff[a] + threadIdx.x];
-    // omega planes of row a (bit 0, bit 1, >= 4), indexed by word - WLO
+    // omega planes of row a (bits 0, 1, 2 of min(omega, 7)), indexed by word - WLO
     const uint32_t* AR = g.dbits + dboff + (int64_t)(ad - dbase) * 3 * WN;
     if (threadIdx.x == 0) row_next = rb;
     __syncthreads();
@@ -625,9 +626,9 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         const int64_t w = inr ? w0 + lane : WHI - 1;
         const int64_t wl = w - WLO;
         // omega_ak and omega_bk of the 32 candidates of word w, as planes
-        const uint32_t qa0 = __ldg(&AR[wl]), qa1 = __ldg(&AR[WN + wl]), qav = __ldg(&AR[2 * WN + wl]);
-        const uint32_t qb0 = __ldg(&BR[wl]), qb1 = __ldg(&BR[WN + wl]), qbv = __ldg(&BR[2 * WN + wl]);
-        uint32_t m = inr ? ((qa0 | qa1 | qav) & (qb0 | qb1 | qbv)) : 0u;
+        const uint32_t qa0 = __ldg(&AR[wl]), qa1 = __ldg(&AR[WN + wl]), qa2 = __ldg(&AR[2 * WN + wl]);
+        const uint32_t qb0 = __ldg(&BR[wl]), qb1 = __ldg(&BR[WN + wl]), qb2 = __ldg(&BR[2 * WN + wl]);
+        uint32_t m = inr ? ((qa0 | qa1 | qa2) & (qb0 | qb1 | qb2)) : 0u;
         if (w == fw) m &= 0xffffffffu << (first & 31);
         // xt = |e_a & e_b & e_k|, bit-sliced (3 bits and an overflow flag)
         uint32_t t0 = 0, t1 = 0, t2 = 0, ovf = 0;
@@ -666,12 +667,12 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
             __syncwarp();
           }
         }
-        // omega >= 4 or xt >= 8: classified from node lists below
-        ovf = (ovf | qav | qbv) & m;
+        // omega >= 7 or xt >= 8: classified from node lists below
+        ovf = (ovf | (qa0 & qa1 & qa2) | (qb0 & qb1 & qb2)) & m;
         const uint32_t valid = m & ~ovf;
-        // on valid bits omega is 1..3: (bit1, bit0) = 01, 10 or 11
-        const uint32_t a1m = qa0 & ~qa1, a2m = ~qa0 & qa1;
-        const uint32_t b1m = qb0 & ~qb1, b2m = ~qb0 & qb1, b3m = qb0 & qb1;
+        // omega = 1, 2, 3 on valid bits
+        const uint32_t a1m = qa0 & ~qa1 & ~qa2, a2m = ~qa0 & qa1 & ~qa2;
+        const uint32_t b1m = qb0 & ~qb1 & ~qb2, b2m = ~qb0 & qb1 & ~qb2, b3m = qb0 & qb1 & ~qb2;
         const uint32_t zt = t0 | t1 | t2;
         const uint32_t one_t = t0 & ~t1 & ~t2;
         // (xa, xb, xt) = (omega_ak - xt, omega_bk - xt, xt)
@@ -743,8 +744,10 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
             src &= 31;
             const int ex = __shfl_sync(0xffffffffu, incl - rc, src);
             const uint32_t rs = __shfl_sync(0xffffffffu, rest, src);
-            const uint32_t sa0 = __shfl_sync(0xffffffffu, qa0, src), sa1 = __shfl_sync(0xffffffffu, qa1, src);
-            const uint32_t sb0 = __shfl_sync(0xffffffffu, qb0, src), sb1 = __shfl_sync(0xffffffffu, qb1, src);
+            const uint32_t sa0 = __shfl_sync(0xffffffffu, qa0, src), sa1 = __shfl_sync(0xffffffffu, qa1, src),
+                           sa2 = __shfl_sync(0xffffffffu, qa2, src);
+            const uint32_t sb0 = __shfl_sync(0xffffffffu, qb0, src), sb1 = __shfl_sync(0xffffffffu, qb1, src),
+                           sb2 = __shfl_sync(0xffffffffu, qb2, src);
             const uint32_t st0 = __shfl_sync(0xffffffffu, t0, src), st1 = __shfl_sync(0xffffffffu, t1, src),
                            st2 = __shfl_sync(0xffffffffu, t2, src);
             const uint32_t sp0 = __shfl_sync(0xffffffffu, p0, src), sp1 = __shfl_sync(0xffffffffu, p1, src),
@@ -756,8 +759,8 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
             if (act) {
               const int bit = __fns(rs, 0, item - ex + 1);
               xt = sval3(st0, st1, st2, bit);
-              xa = (int)((sa0 >> bit) & 1u) + 2 * (int)((sa1 >> bit) & 1u) - xt;
-              xb = (int)((sb0 >> bit) & 1u) + 2 * (int)((sb1 >> bit) & 1u) - xt;
+              xa = sval3(sa0, sa1, sa2, bit) - xt;
+              xb = sval3(sb0, sb1, sb2, bit) - xt;
               int C = (int)((sp0 >> bit) & 1u) | ((int)((sp1 >> bit) & 1u) << 1) |
                       ((int)((sp2 >> bit) & 1u) << 2) | ((int)((sp3 >> bit) & 1u) << 3);
               if (C >= 15) C = g.dsize[sw * 32 + bit];
@@ -963,7 +966,7 @@ __global__ void __launch_bounds__(kThreads) k_sparse_triangles(SplitArgs g, int 
       __syncwarp();
       if (bd >= 0) {
         // b dense: every k after b is dense with a larger dense index
-        // omega planes of row b: omega_bk = bit0 + 2 bit1, or >= 4
+        // omega planes of row b: omega_bk = bit0 + 2 bit1 + 4 bit2 (7: 7 or more)
         const uint32_t* Q = g.dbits + dboff + (int64_t)(bd - dbase) * 3 * WN;
         for (int q = lane; q < deg; q += 32) {
           const int kd = sdi[q];
@@ -971,12 +974,12 @@ __global__ void __launch_bounds__(kThreads) k_sparse_triangles(SplitArgs g, int 
           const uint32_t bit = 1u << (kd & 31);
           const int64_t wq = (kd >> 5) - WLO;
           const uint32_t q0 = __ldg(&Q[wq]) & bit, q1 = __ldg(&Q[WN + wq]) & bit,
-                         qv = __ldg(&Q[2 * WN + wq]) & bit;
-          if (!(q0 | q1 | qv)) continue;
+                         q2 = __ldg(&Q[2 * WN + wq]) & bit;
+          if (!(q0 | q1 | q2)) continue;
           const int64_t k = skey[q];
           const int C = ssz[q];
-          int y = (q0 ? 1 : 0) + (q1 ? 2 : 0);
-          if (qv) y = sorted_overlap(bnodes, B, g.enode + g.eoff[k], C);
+          int y = (q0 ? 1 : 0) + (q1 ? 2 : 0) + (q2 ? 4 : 0);
+          if (y == 7) y = sorted_overlap(bnodes, B, g.enode + g.eoff[k], C);
           const int z = entry_omega(sw1[q], A);
           int t;
           if (A <= kMaskedMax) {
@@ -1098,15 +1101,12 @@ __global__ void k_dense_bits(int64_t n_dense, const SegInfo* __restrict__ seg,
       const uint2 e = nadj[p];
       const int kd = didx[ent_id(e)];
       if (kd < 0) continue;
-      const int om = entry_omega(e.y, B);
+      const int om = min(entry_omega(e.y, B), 7);   // 7 stands for 7 or more
       const int64_t wq = (kd >> 5) - sg.wlo;
       const uint32_t bit = 1u << (kd & 31);
-      if (om >= 4) {
-        atomicOr(&Q[2 * sg.wn + wq], bit);
-      } else {
-        if (om & 1) atomicOr(&Q[wq], bit);
-        if (om & 2) atomicOr(&Q[sg.wn + wq], bit);
-      }
+      if (om & 1) atomicOr(&Q[wq], bit);
+      if (om & 2) atomicOr(&Q[sg.wn + wq], bit);
+      if (om & 4) atomicOr(&Q[2 * sg.wn + wq], bit);
     }
   }
 }
