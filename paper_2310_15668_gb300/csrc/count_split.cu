@@ -294,15 +294,14 @@ constexpr int kSlots = 8;          // per-warp signature slots of popcounted bin
 constexpr uint32_t kSlotFlush = 1024;   // hyperwedges per slot before it is flushed
 
 struct WarpScratch {
-  int64_t lpos[128];     // next unread entry of each light node's dense list
-  int64_t lend[128];     // end of that list
-  int32_t lnext[128];    // dense index at lpos (INT_MAX when done)
-  int32_t lent[kLight];  // merged entries (dense index << 2 | group), ascending
+  int64_t lpos[64];      // next unread entry of each light node's dense list
+  int64_t lend[64];      // end of that list
+  int32_t lnext[64];     // dense index at lpos (INT_MAX when done)
+  int32_t lent[kLight];  // merged entries (dense indices), ascending
   int32_t bnodes[64];
-  int32_t hidx[3][64];   // heavy indices of groups A, B, T
-  int32_t light[128];    // light nodes of e_a | e_b
-  int32_t lgrp[128];     // their group (0 A, 1 B, 2 T)
-  int32_t n[6];          // nA, nB, nT, nlight, pad
+  int32_t hidx[64];      // heavy indices of the nodes of e_a & e_b
+  int32_t light[64];     // the nodes of e_a & e_b without a bitmap
+  int32_t n[2];          // how many of each
   uint32_t table[kCombo * kCeff];
   uint32_t dirty[kCombo * kCeff / 32];
   // theta = 1: totals of the popcounted bins summed over the row's
@@ -326,76 +325,22 @@ __device__ __forceinline__ void slice_add(uint32_t& c0, uint32_t& c1, uint32_t& 
   c2 ^= k1;
 }
 
-__device__ __forceinline__ uint32_t eq3(uint32_t c0, uint32_t c1, uint32_t c2, int v) {
-  return ((v & 1) ? c0 : ~c0) & ((v & 2) ? c1 : ~c1) & ((v & 4) ? c2 : ~c2);
-}
-
 __device__ __forceinline__ int sval3(uint32_t c0, uint32_t c1, uint32_t c2, int bit) {
   return (int)((c0 >> bit) & 1u) + 2 * (int)((c1 >> bit) & 1u) + 4 * (int)((c2 >> bit) & 1u);
 }
 
-// lanes (bits) whose 2-bit sliced value equals v
-__device__ __forceinline__ uint32_t eq2(uint32_t c0, uint32_t c1, int v) {
-  return ((v & 1) ? c0 : ~c0) & ((v & 2) ? c1 : ~c1);
-}
-
-// bits whose 4-bit value (planes p0..p3) equals / is at least k
-__device__ __forceinline__ uint32_t eq4(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3, int k) {
-  return ((k & 1) ? p0 : ~p0) & ((k & 2) ? p1 : ~p1) & ((k & 4) ? p2 : ~p2) & ((k & 8) ? p3 : ~p3);
-}
-
-__device__ __forceinline__ uint32_t ge4(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3, int k) {
-  const uint32_t pl[4] = {p0, p1, p2, p3};
-  uint32_t gt = 0u, eq = 0xffffffffu;
-#pragma unroll
-  for (int b = 3; b >= 0; --b) {
-    if ((k >> b) & 1) {
-      eq &= pl[b];
-    } else {
-      gt |= eq & pl[b];
-      eq &= ~pl[b];
-    }
-  }
-  return gt | eq;
-}
-
-__device__ __forceinline__ int sval(uint32_t c0, uint32_t c1, int bit) {
-  return (int)((c0 >> bit) & 1u) + 2 * (int)((c1 >> bit) & 1u);
-}
-
-// Per-warp table of (combination, effective size) counts for the rarer
-// combinations; counts of 4 or more in a group, or sizes beyond the table,
-// are added to the histogram directly.
-template <typename WS>
-__device__ __forceinline__ void table_add(WS& me, int combo3, int ce, uint32_t n,
-                                          unsigned long long* hist, const uint16_t* lut, int theta,
-                                          int A, int B, int x, int xa, int xb, int xt) {
-  if (xa < 4 && xb < 4 && xt < 4 && ce >= 1 && ce <= kCeff) {
-    const int key = ((xa * 4 + xb) * 4 + xt) * kCeff + ce - 1;
-    atomicAdd(&me.table[key], n);
-    atomicOr(&me.dirty[key >> 5], 1u << (key & 31));
-  } else {
-    add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, (long long)n);
-  }
-  (void)combo3;
-}
-
-// exact overlaps of e_k with e_a and e_b (and the part through heavy nodes)
+// exact overlaps of e_k with e_a (z), e_b (y) and both (t)
 struct Overlap {
-  int z, y, t, hz, hy, ht;
+  int z, y, t;
 };
 
 __device__ __forceinline__ Overlap overlaps(const int32_t* anodes, int A, const int32_t* bnodes,
-                                            int B, const int32_t* knodes, int C,
-                                            const int32_t* heavy_idx) {
-  Overlap o{0, 0, 0, 0, 0, 0};
+                                            int B, const int32_t* knodes, int C) {
+  Overlap o{0, 0, 0};
   for (int q = 0; q < C; ++q) {
     const int32_t u = knodes[q];
     const bool ia = has_node(anodes, A, u), ib = has_node(bnodes, B, u);
-    if (!ia && !ib) continue;
-    const bool hv = heavy_idx[u] >= 0;
     o.z += ia; o.y += ib; o.t += ia && ib;
-    if (hv) { o.hz += ia; o.hy += ib; o.ht += ia && ib; }
   }
   return o;
 }
@@ -542,7 +487,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       const int x = entry_omega(eab.y, A);
       if (lane < B) me.bnodes[lane] = g.enode[g.eoff[b] + lane];
       if (lane + 32 < B) me.bnodes[lane + 32] = g.enode[g.eoff[b] + lane + 32];
-      if (lane < 5) me.n[lane] = 0;
+      if (lane < 2) me.n[lane] = 0;
       __syncwarp();
       // the nodes of e_a & e_b (group T): with a bitmap ("heavy") or a short
       // list of dense hyperedges ("light")
@@ -554,17 +499,17 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         const bool hvy = inT && hv >= 0, lt = inT && hv < 0;
         const unsigned bh = __ballot_sync(0xffffffffu, hvy);
         const unsigned bl = __ballot_sync(0xffffffffu, lt);
-        const int nh0 = me.n[2], nl0 = me.n[3];
-        if (hvy) me.hidx[2][nh0 + __popc(bh & ((1u << lane) - 1u))] = hv - (int)hbase;
+        const int nh0 = me.n[0], nl0 = me.n[1];
+        if (hvy) me.hidx[nh0 + __popc(bh & ((1u << lane) - 1u))] = hv - (int)hbase;
         if (lt) me.light[nl0 + __popc(bl & ((1u << lane) - 1u))] = u;
         __syncwarp();
         if (lane == 0) {
-          me.n[2] = nh0 + __popc(bh);
-          me.n[3] = nl0 + __popc(bl);
+          me.n[0] = nh0 + __popc(bh);
+          me.n[1] = nl0 + __popc(bl);
         }
         __syncwarp();
       }
-      const int nT = me.n[2], nL = me.n[3];
+      const int nT = me.n[0], nL = me.n[1];
       const uint32_t* BR = g.dbits + dboff + (int64_t)(bd - dbase) * 3 * WN;
       // per-lane counters: 14 pairs of 16-bit bins (theta = 1) or 10 bins
       uint32_t cnt[14];
@@ -633,7 +578,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         // xt = |e_a & e_b & e_k|, bit-sliced (3 bits and an overflow flag)
         uint32_t t0 = 0, t1 = 0, t2 = 0, ovf = 0;
         for (int h = 0; h < nT; ++h)
-          slice_add(t0, t1, t2, ovf, __ldg(&NB[(int64_t)me.hidx[2][h] * WN + wl]));
+          slice_add(t0, t1, t2, ovf, __ldg(&NB[(int64_t)me.hidx[h] * WN + wl]));
         // light T nodes with a dense index in this iteration's 32 words
         const int64_t hi64 = (w0 + 32) * 32;
         const int32_t hi = hi64 < 0x7fffffff ? (int32_t)hi64 : 0x7fffffff;
@@ -787,7 +732,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
           const int64_t k = g.dense_row[w * 32 + bit];
           const int64_t kb = g.eoff[k];
           const int C = (int)(g.eoff[k + 1] - kb);
-          const Overlap o = overlaps(anodes, A, me.bnodes, B, g.enode + kb, C, g.heavy_idx);
+          const Overlap o = overlaps(anodes, A, me.bnodes, B, g.enode + kb, C);
           add_triangle(hist, lut, theta, A, B, C, x, o.y, o.z, o.t, 1);
         }
       }
