@@ -569,33 +569,37 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
       // the overlap planes of the 32 candidates of word w (omega_ak, omega_bk)
       // and their size planes are loaded one iteration ahead, so that a
       // warp has the next chunk's loads in flight while it works on this one
+      // (and the bitmap word of the first heavy node of e_a & e_b, if any)
+      const uint32_t* T0 = NB + (nT > 0 ? (int64_t)me.hidx[0] * WN : 0);
       uint32_t nqa0 = 0, nqa1 = 0, nqa2 = 0, nqb0 = 0, nqb1 = 0, nqb2 = 0;
-      uint32_t np0 = 0, np1 = 0, np2 = 0, np3 = 0;
+      uint32_t np0 = 0, np1 = 0, np2 = 0, np3 = 0, nt = 0;
       if (fw < WHI) {
         const int64_t w = fw + lane < WHI ? fw + lane : WHI - 1;
         const int64_t wl = w - WLO;
         nqa0 = __ldg(&AR[wl]); nqa1 = __ldg(&AR[WN + wl]); nqa2 = __ldg(&AR[2 * WN + wl]);
         nqb0 = __ldg(&BR[wl]); nqb1 = __ldg(&BR[WN + wl]); nqb2 = __ldg(&BR[2 * WN + wl]);
         np0 = __ldg(&P0[w]); np1 = __ldg(&P1[w]); np2 = __ldg(&P2[w]); np3 = __ldg(&P3[w]);
+        if (nT > 0) nt = __ldg(&T0[wl]);
       }
       for (int64_t w0 = fw; w0 < WHI; w0 += 32) {
         const bool inr = w0 + lane < WHI;
         const int64_t w = inr ? w0 + lane : WHI - 1;
         const int64_t wl = w - WLO;
         const uint32_t qa0 = nqa0, qa1 = nqa1, qa2 = nqa2, qb0 = nqb0, qb1 = nqb1, qb2 = nqb2;
-        const uint32_t p0 = np0, p1 = np1, p2 = np2, p3 = np3;
+        const uint32_t p0 = np0, p1 = np1, p2 = np2, p3 = np3, tb = nt;
         {
           const int64_t w1 = w0 + 32 + lane < WHI ? w0 + 32 + lane : WHI - 1;
           const int64_t wl1 = w1 - WLO;
           nqa0 = __ldg(&AR[wl1]); nqa1 = __ldg(&AR[WN + wl1]); nqa2 = __ldg(&AR[2 * WN + wl1]);
           nqb0 = __ldg(&BR[wl1]); nqb1 = __ldg(&BR[WN + wl1]); nqb2 = __ldg(&BR[2 * WN + wl1]);
           np0 = __ldg(&P0[w1]); np1 = __ldg(&P1[w1]); np2 = __ldg(&P2[w1]); np3 = __ldg(&P3[w1]);
+          if (nT > 0) nt = __ldg(&T0[wl1]);
         }
         uint32_t m = inr ? ((qa0 | qa1 | qa2) & (qb0 | qb1 | qb2)) : 0u;
         if (w == fw) m &= 0xffffffffu << (first & 31);
         // xt = |e_a & e_b & e_k|, bit-sliced (3 bits and an overflow flag)
-        uint32_t t0 = 0, t1 = 0, t2 = 0, ovf = 0;
-        for (int h = 0; h < nT; ++h)
+        uint32_t t0 = tb, t1 = 0, t2 = 0, ovf = 0;   // tb: the first heavy node's word
+        for (int h = 1; h < nT; ++h)
           slice_add(t0, t1, t2, ovf, __ldg(&NB[(int64_t)me.hidx[h] * WN + wl]));
         // light T nodes with a dense index in this iteration's 32 words
         const int64_t hi64 = (w0 + 32) * 32;
