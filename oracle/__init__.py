@@ -135,6 +135,20 @@ def count_exact(offsets, nodes, theta: int = 1):
     return h, h3
 
 
+def hyperedge_profile(offsets, nodes, theta: int = 1):
+    """Hyperedge profiles (Section 3.1, "Hyperedge Profile (HP)"): row e
+    counts the instances of each h-motif / 3h-motif that include hyperedge e
+    (ids after duplicate removal).  Returns (hp_h [E, 26], hp_3h [E, 431])."""
+    off, nod = _csr(offsets, nodes)
+    e_kept = dedupe(off, nod)[0].size - 1
+    hp_h = np.zeros((max(e_kept, 1), N_H), np.int64)
+    hp_3h = np.zeros((max(e_kept, 1), N_3H), np.int64)
+    _check(_load().orc_hyperedge_profile(ctypes.c_int64(off.size - 1), _p(off), _p(nod),
+                                         ctypes.c_int32(theta), _p(hp_h), _p(hp_3h)),
+           "hyperedge_profile")
+    return hp_h[:e_kept], hp_3h[:e_kept]
+
+
 def count_exact_subset(offsets, nodes, anchors, theta: int = 1):
     off, nod = _csr(offsets, nodes)
     anc = np.ascontiguousarray(anchors, dtype=np.int32)

@@ -335,9 +335,13 @@ void classify(const std::array<int64_t, 7>& r, int32_t theta, int* h, int* h3) {
 // Algorithm "exact_motif_counting" (MoCHy-E): for each e_i, each unordered
 // pair {e_j, e_k} of its neighbours, count it when e_j and e_k are disjoint
 // or i < min(j, k).  Restricted to the anchors in `only` when non-null.
+// With hp_h / hp_3h (|E| x 26 / |E| x 431, may be null) every counted
+// instance is also added to the rows of its three hyperedges: the hyperedge
+// profile (Section 3.1, "Hyperedge Profile (HP)": the t-th element of HP(e)
+// is the number of instances of motif t that include e).
 void exact_count(const Hypergraph& G, const LineGraph& L, int32_t theta,
                  const std::vector<int32_t>* only, int64_t* out_h,
-                 int64_t* out_3h) {
+                 int64_t* out_3h, int64_t* hp_h = nullptr, int64_t* hp_3h = nullptr) {
   std::fill(out_h, out_h + 26, 0);
   std::fill(out_3h, out_3h + 431, 0);
   const int64_t E = (int64_t)G.e.size();
@@ -359,6 +363,10 @@ void exact_count(const Hypergraph& G, const LineGraph& L, int32_t theta,
         classify(r, theta, &h, &h3);
         out_h[h - 1] += 1;
         out_3h[h3 - 1] += 1;
+        for (int32_t e : {i, j, k}) {
+          if (hp_h) hp_h[(int64_t)e * 26 + h - 1] += 1;
+          if (hp_3h) hp_3h[(int64_t)e * 431 + h3 - 1] += 1;
+        }
       }
   }
 }
@@ -605,6 +613,23 @@ int orc_count_exact(int64_t n_edges, const int64_t* off, const int32_t* nodes,
   if (build(n_edges, off, nodes, G)) return -1;
   LineGraph L = project(G);
   exact_count(G, L, theta, nullptr, out_h, out_3h);
+  return 0;
+}
+
+// Hyperedge profiles (Section 3.1, "Hyperedge Profile (HP)") of every
+// hyperedge, from the instances of Algorithm "exact_motif_counting":
+// hp_h is |E| x 26, hp_3h is |E| x 431 (row e = hyperedge e after duplicate
+// removal); either may be null.
+int orc_hyperedge_profile(int64_t n_edges, const int64_t* off, const int32_t* nodes,
+                          int32_t theta, int64_t* hp_h, int64_t* hp_3h) {
+  Hypergraph G;
+  if (build(n_edges, off, nodes, G)) return -1;
+  LineGraph L = project(G);
+  const int64_t E = (int64_t)G.e.size();
+  if (hp_h) std::fill(hp_h, hp_h + E * 26, 0);
+  if (hp_3h) std::fill(hp_3h, hp_3h + E * 431, 0);
+  int64_t h[26], h3[431];
+  exact_count(G, L, theta, nullptr, h, h3, hp_h, hp_3h);
   return 0;
 }
 
