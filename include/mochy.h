@@ -132,6 +132,17 @@ int mochy_count_exact_subset(mochy_ctx* ctx, const int32_t* h_anchors,
                              int64_t n_anchors, int64_t out_h[MOCHY_N_H],
                              int64_t out_3h[MOCHY_N_3H]);
 
+/* Hyperedge profiles (Section 3.1, "Hyperedge Profile (HP)"; Section 4.1
+ * for their 3h-motif form): hp_h[e * 26 + t - 1] is the number of instances
+ * of h-motif t that include hyperedge e, hp_3h[e * 431 + t - 1] the same for
+ * 3h-motif t (host arrays of n_edges rows; either may be NULL).  Instances
+ * are enumerated one by one (the per-hyperwedge scan of MoCHy-E, each
+ * attributed to its three hyperedges), so the call suits hypergraphs of up
+ * to about 1e10 connected triples and at most 786,432 hyperedges; it needs
+ * mochy_project and 3.5 KB of device memory per hyperedge while it runs.
+ * Summed over hyperedges, the profiles are three times the motif counts. */
+int mochy_hyperedge_profile(mochy_ctx* ctx, int64_t* hp_h, int64_t* hp_3h);
+
 /* Sampled counts.  method MOCHY_A draws `samples` hyperedges uniformly with
  * replacement (Algorithm "sampling_ver1"); MOCHY_A_PLUS draws `samples`
  * hyperwedges (Algorithm "sampling_ver2").  Draw n uses Philox4x32-10 with

@@ -30,6 +30,7 @@ EXPORTS = [
     "mochy_motif_pattern", "mochy_stream", "mochy_device_bytes", "mochy_kernel_launches",
     "mochy_strerror", "mochy_last_error", "mochy_trace", "mochy_trace_read",
     "mochy_count_sampled_noalloc", "mochy_profile_batch", "mochy_server_create",
+    "mochy_hyperedge_profile",
     "mochy_server_submit", "mochy_server_poll", "mochy_server_stats", "mochy_server_destroy",
 ]
 MOCHY_REQ_EXACT, MOCHY_REQ_SAMPLED, MOCHY_REQ_PROFILE = 1, 2, 3
@@ -145,6 +146,7 @@ def load_library(path: str = LIB_PATH):
             lib.mochy_profile_batch.argtypes = [ctypes.POINTER(mochy_config), i32, vp, vp, vp, vp,
                                                 i32, vp, vp, vp, vp, vp, vp, vp, vp,
                                                 ctypes.POINTER(mochy_batch_info)]
+            lib.mochy_hyperedge_profile.argtypes = [vp, vp, vp]
             lib.mochy_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(mochy_config),
                                                 i32, i32]
             lib.mochy_server_submit.argtypes = [vp, ctypes.POINTER(mochy_request),
@@ -283,6 +285,15 @@ def mochy_profile(ctx: int, n_random: int, seed: int):
                 degenerate=rc == W_DEGENERATE_CP)
 
 
+def mochy_hyperedge_profile(ctx: int, n_edges: int):
+    """Hyperedge profiles of the projected hypergraph: (hp_h [E, 26], hp_3h [E, 431])."""
+    hp_h = np.zeros((max(n_edges, 1), N_H), np.int64)
+    hp_3h = np.zeros((max(n_edges, 1), N_3H), np.int64)
+    _check(load_library().mochy_hyperedge_profile(ctx, _p(hp_h), _p(hp_3h)),
+           "mochy_hyperedge_profile")
+    return hp_h[:n_edges], hp_3h[:n_edges]
+
+
 def mochy_profile_batch(graphs, n_random: int, seeds, cfg: mochy_config | None = None):
     """Profiles of several hypergraphs at once.  graphs: list of
     (n_nodes, offsets, nodes); seeds: one per graph.  Returns
@@ -394,6 +405,10 @@ class Context:
 
     def profile(self, n_random, seed):
         return mochy_profile(self.h, n_random, seed)
+
+    def hyperedge_profile(self):
+        _, off, _ = self.hypergraph()
+        return mochy_hyperedge_profile(self.h, off.size - 1)
 
     def hypergraph(self):
         return mochy_get_hypergraph(self.h)

@@ -118,6 +118,103 @@ k_exact_rows(ExactArgs g) {
     if (hist[q]) atomicAdd(&g.hist[q], hist[q]);
 }
 
+// Hyperedge profiles (Section 3.1, "Hyperedge Profile (HP)": the t-th
+// element of HP(e) is the number of instances of motif t that include e).
+// The instances are enumerated exactly as by k_exact_rows (each once, from
+// the CTA of its smallest leaf or smallest member e_a) and each is added to
+// the profiles of its three hyperedges: e_a's in a shared row flushed once
+// per staged row, e_b's through a per-lane run cache flushed per
+// hyperwedge, e_k's by a global atomic.  hp is |E| x 432 (index = 3h id).
+__global__ void __launch_bounds__(kExactThreads)
+k_hyperedge_profile(ExactArgs g, unsigned long long* __restrict__ hp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* hista = (unsigned long long*)smem;
+  uint16_t* lut = (uint16_t*)(hista + 432);
+  int32_t* anodes = (int32_t*)(lut + 2192);
+  uint32_t* codes = (uint32_t*)(anodes + 64);
+  __shared__ int64_t row_slot;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t code_words = (g.n_edges + 15) / 16;
+  for (int q = threadIdx.x; q < 432; q += kExactThreads) hista[q] = 0ull;
+  for (int q = threadIdx.x; q < 2187; q += kExactThreads) lut[q] = g.lut3[q];
+  while (true) {
+    if (threadIdx.x == 0) row_slot = atomicAdd(g.queue, 1);
+    __syncthreads();
+    const int64_t slot = row_slot;
+    if (slot >= g.n_rows) break;
+    const int64_t a = g.rows[slot];
+    const int64_t ab = g.noff[a], ae = g.noff[a + 1];
+    const int A = (int)(g.eoff[a + 1] - g.eoff[a]);
+    if (threadIdx.x < A) anodes[threadIdx.x] = g.enode[g.eoff[a] + threadIdx.x];
+    for (int64_t q = threadIdx.x; q < code_words; q += kExactThreads) codes[q] = 0u;
+    __syncthreads();
+    for (int64_t p = ab + threadIdx.x; p < ae; p += kExactThreads) {
+      const uint2 e = g.nadj[p];
+      const uint32_t k = ent_id(e);
+      const uint32_t w = (uint32_t)min(entry_omega(e.y, A), 3);
+      atomicOr(&codes[k >> 4], w << (2 * (k & 15)));
+    }
+    __syncthreads();
+    for (int64_t idx = ab + warp; idx < ae; idx += kExactWarps) {
+      const uint2 eab = g.nadj[idx];
+      const uint32_t b = ent_id(eab);
+      const int B = ent_size(eab);
+      const int x = entry_omega(eab.y, A);
+      const int64_t bb = g.noff[b], be = g.noff[b + 1];
+      const int64_t pa = warp_lower_bound(g.nadj, bb, be, (uint32_t)a);
+      const uint32_t mask_ba = g.nadj[pa].y;   // nodes of e_b lying in e_a
+      const bool b_after_a = (int64_t)b > a;
+      unsigned long long* hpb = hp + (int64_t)b * 432;
+      RunCache rcb;
+      for (int64_t q = pa + 1 + lane; q < be; q += 32) {
+        const uint2 ebk = g.nadj[q];
+        const uint32_t k = ent_id(ebk);
+        const int C = ent_size(ebk);
+        const int y = entry_omega(ebk.y, B);
+        const int za = (int)((codes[k >> 4] >> (2 * (k & 15))) & 3u);
+        int code;
+        if (za == 0) {
+          // open, centre b, leaves a < k
+          code = ternary_code(A, B, C, x, y, 0, 0, g.theta);
+        } else if (b_after_a && k > b) {
+          // closed, a < b < k
+          int z = za;
+          if (za == 3) {
+            const int64_t kb = g.eoff[k];
+            z = sorted_overlap(anodes, A, g.enode + kb, (int)(g.eoff[k + 1] - kb));
+          }
+          int t;
+          if (B <= kMaskedMax) {
+            t = __popc(mask_ba & ebk.y);
+          } else {
+            const int64_t kb = g.eoff[k], bb2 = g.eoff[b];
+            t = sorted_overlap3(anodes, A, g.enode + bb2, B, g.enode + kb,
+                                (int)(g.eoff[k + 1] - kb));
+          }
+          code = ternary_code(A, B, C, x, y, z, t, g.theta);
+        } else {
+          continue;
+        }
+        const int id = lut[code];
+        atomicAdd(&hista[id], 1ull);
+        rcb.add(id, hpb);
+        atomicAdd(&hp[(int64_t)k * 432 + id], 1ull);
+      }
+      rcb.flush(hpb);
+    }
+    __syncthreads();
+    unsigned long long* hpa = hp + a * 432;
+    for (int q = threadIdx.x; q < 432; q += kExactThreads) {
+      const unsigned long long v = hista[q];
+      if (v) {
+        atomicAdd(&hpa[q], v);
+        hista[q] = 0ull;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Test hook: the contribution of the outer-loop iterations of the given
 // anchors in Algorithm exact_motif_counting.  For anchor e_x, every pair
 // {p, q} of its neighbours with p < q is checked: counted when p and q are
@@ -181,6 +278,41 @@ k_exact_anchor(ExactArgs g, const int32_t* __restrict__ anchors, int64_t n_ancho
 
 size_t exact_smem_bytes(int64_t n_edges) {
   return 432 * 8 + 2192 * 2 + 64 * 4 + (size_t)((n_edges + 15) / 16) * 4;
+}
+
+// The hyperedge profiles of the projected hypergraph into d_hp (|E| x 432,
+// cleared here).
+int hyperedge_profiles(mochy_ctx* ctx, unsigned long long* d_hp) {
+  if (!ctx->projected) return fail(MOCHY_E_NOT_PROJECTED, "call mochy_project first");
+  cudaStream_t st = ctx->stream;
+  const int64_t E = ctx->n_edges;
+  if (E == 0) return MOCHY_OK;
+  MOCHY_CUDA(cudaMemsetAsync(d_hp, 0, (size_t)E * 432 * 8, st));
+  MOCHY_CUDA(cudaMemsetAsync(ctx->counters, 0, 16 * sizeof(int32_t), st));
+  ExactArgs g;
+  g.n_edges = E;
+  g.eoff = ctx->eoff;
+  g.enode = ctx->enode;
+  g.noff = ctx->noff;
+  g.nadj = ctx->nadj;
+  g.rows = ctx->row_order;
+  g.n_rows = E;
+  g.queue = ctx->counters + 4;
+  g.lut3 = ctx->tables.lut3;
+  g.hist = nullptr;
+  g.theta = ctx->theta;
+  const size_t smem = exact_smem_bytes(E);
+  if (smem + 1024 > ctx->smem_optin)
+    return fail(MOCHY_E_UNSUPPORTED, "hyperedge profiles support at most 786432 hyperedges");
+  MOCHY_TRY(ensure_dynamic_smem((const void*)k_hyperedge_profile, smem));
+  int per_sm = 0;
+  MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hyperedge_profile,
+                                                           kExactThreads, smem));
+  per_sm = std::max(per_sm, 1);
+  const unsigned grid = (unsigned)std::min<int64_t>((int64_t)ctx->num_sms * per_sm, E);
+  k_hyperedge_profile<<<grid, kExactThreads, smem, st>>>(g, d_hp);
+  MOCHY_LAUNCHED();
+  return MOCHY_OK;
 }
 
 int count_exact(mochy_ctx* ctx, const int32_t* d_anchors, int64_t n_anchors,
