@@ -149,6 +149,19 @@ def hyperedge_profile(offsets, nodes, theta: int = 1):
     return hp_h[:e_kept], hp_3h[:e_kept]
 
 
+def star_node_profile(n_nodes: int, offsets, nodes, theta: int = 1):
+    """Star node profiles (Section 3.1, "Node Profile (NP)", star
+    ego-networks): row v counts the instances of each h-motif / 3h-motif
+    among the hyperedges that contain v.  Returns (np_h [N, 26], np_3h [N, 431])."""
+    off, nod = _csr(offsets, nodes)
+    np_h = np.zeros((max(n_nodes, 1), N_H), np.int64)
+    np_3h = np.zeros((max(n_nodes, 1), N_3H), np.int64)
+    _check(_load().orc_star_node_profile(ctypes.c_int64(n_nodes), ctypes.c_int64(off.size - 1),
+                                         _p(off), _p(nod), ctypes.c_int32(theta), _p(np_h),
+                                         _p(np_3h)), "star_node_profile")
+    return np_h[:n_nodes], np_3h[:n_nodes]
+
+
 def count_exact_subset(offsets, nodes, anchors, theta: int = 1):
     off, nod = _csr(offsets, nodes)
     anc = np.ascontiguousarray(anchors, dtype=np.int32)

@@ -633,6 +633,41 @@ int orc_hyperedge_profile(int64_t n_edges, const int64_t* off, const int32_t* no
   return 0;
 }
 
+// Star node profiles (Section 3.1, "Node Profile (NP)" with the star
+// ego-network of "Hypergraph Ego-networks"): the star ego-network of v keeps
+// the hyperedges that contain v, E_v, whole; its motif instances are the
+// connected triples of E_v (all of them: every pair shares v), classified as
+// in G.  np_h is n_nodes x 26, np_3h is n_nodes x 431; either may be null.
+int orc_star_node_profile(int64_t n_nodes, int64_t n_edges, const int64_t* off,
+                          const int32_t* nodes, int32_t theta, int64_t* np_h,
+                          int64_t* np_3h) {
+  Hypergraph G;
+  if (build(n_edges, off, nodes, G)) return -1;
+  if (np_h) std::fill(np_h, np_h + n_nodes * 26, 0);
+  if (np_3h) std::fill(np_3h, np_3h + n_nodes * 431, 0);
+  auto overlap = [&](int64_t x, int64_t y) {
+    int64_t c = 0;
+    for (int32_t u : G.e[x]) c += G.eset[y].count(u) ? 1 : 0;
+    return c;
+  };
+  for (const auto& kv : G.ev) {
+    const int64_t v = kv.first;
+    if (v < 0 || v >= n_nodes) return -1;
+    const std::vector<int32_t>& Ev = kv.second;
+    for (size_t x = 0; x < Ev.size(); ++x)
+      for (size_t y = x + 1; y < Ev.size(); ++y)
+        for (size_t z = y + 1; z < Ev.size(); ++z) {
+          const int32_t i = Ev[x], j = Ev[y], k = Ev[z];
+          auto r = regions(G, i, j, k, overlap(i, j), overlap(j, k), overlap(k, i));
+          int h, h3;
+          classify(r, theta, &h, &h3);
+          if (np_h) np_h[v * 26 + h - 1] += 1;
+          if (np_3h) np_3h[v * 431 + h3 - 1] += 1;
+        }
+  }
+  return 0;
+}
+
 // MoCHy-E restricted to the outer-loop hyperedges in `anchors`; the line
 // graph rows of the anchors come from the on-the-fly neighbour routine
 // (Appendix "on-the-fly", getNeighbors) and the overlaps of neighbour pairs
