@@ -143,6 +143,17 @@ int mochy_count_exact_subset(mochy_ctx* ctx, const int32_t* h_anchors,
  * Summed over hyperedges, the profiles are three times the motif counts. */
 int mochy_hyperedge_profile(mochy_ctx* ctx, int64_t* hp_h, int64_t* hp_3h);
 
+/* Star node profiles (Section 3.1, "Node Profile (NP)" with the star
+ * ego-network of v: the hyperedges that contain v, kept whole):
+ * np_h[v * 26 + t - 1] / np_3h[v * 431 + t - 1] count the instances of
+ * h-motif / 3h-motif t among those hyperedges (host arrays of n_nodes rows;
+ * either may be NULL).  Every such instance is a closed instance of G whose
+ * triple intersection holds v, so a row sums to C(|E_v|, 3).  Instances are
+ * enumerated one by one, as for mochy_hyperedge_profile (same size limits);
+ * needs mochy_project and 3.5 KB of device memory per node while it runs.
+ * Radial and contracted node profiles are not provided. */
+int mochy_star_node_profile(mochy_ctx* ctx, int64_t* np_h, int64_t* np_3h);
+
 /* Sampled counts.  method MOCHY_A draws `samples` hyperedges uniformly with
  * replacement (Algorithm "sampling_ver1"); MOCHY_A_PLUS draws `samples`
  * hyperwedges (Algorithm "sampling_ver2").  Draw n uses Philox4x32-10 with

@@ -30,7 +30,7 @@ EXPORTS = [
     "mochy_motif_pattern", "mochy_stream", "mochy_device_bytes", "mochy_kernel_launches",
     "mochy_strerror", "mochy_last_error", "mochy_trace", "mochy_trace_read",
     "mochy_count_sampled_noalloc", "mochy_profile_batch", "mochy_server_create",
-    "mochy_hyperedge_profile",
+    "mochy_hyperedge_profile", "mochy_star_node_profile",
     "mochy_server_submit", "mochy_server_poll", "mochy_server_stats", "mochy_server_destroy",
 ]
 MOCHY_REQ_EXACT, MOCHY_REQ_SAMPLED, MOCHY_REQ_PROFILE = 1, 2, 3
@@ -147,6 +147,7 @@ def load_library(path: str = LIB_PATH):
                                                 i32, vp, vp, vp, vp, vp, vp, vp, vp,
                                                 ctypes.POINTER(mochy_batch_info)]
             lib.mochy_hyperedge_profile.argtypes = [vp, vp, vp]
+            lib.mochy_star_node_profile.argtypes = [vp, vp, vp]
             lib.mochy_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(mochy_config),
                                                 i32, i32]
             lib.mochy_server_submit.argtypes = [vp, ctypes.POINTER(mochy_request),
@@ -294,6 +295,15 @@ def mochy_hyperedge_profile(ctx: int, n_edges: int):
     return hp_h[:n_edges], hp_3h[:n_edges]
 
 
+def mochy_star_node_profile(ctx: int, n_nodes: int):
+    """Star node profiles of the projected hypergraph: (np_h [N, 26], np_3h [N, 431])."""
+    np_h = np.zeros((max(n_nodes, 1), N_H), np.int64)
+    np_3h = np.zeros((max(n_nodes, 1), N_3H), np.int64)
+    _check(load_library().mochy_star_node_profile(ctx, _p(np_h), _p(np_3h)),
+           "mochy_star_node_profile")
+    return np_h[:n_nodes], np_3h[:n_nodes]
+
+
 def mochy_profile_batch(graphs, n_random: int, seeds, cfg: mochy_config | None = None):
     """Profiles of several hypergraphs at once.  graphs: list of
     (n_nodes, offsets, nodes); seeds: one per graph.  Returns
@@ -409,6 +419,10 @@ class Context:
     def hyperedge_profile(self):
         _, off, _ = self.hypergraph()
         return mochy_hyperedge_profile(self.h, off.size - 1)
+
+    def star_node_profile(self):
+        n_nodes, _, _ = self.hypergraph()
+        return mochy_star_node_profile(self.h, n_nodes)
 
     def hypergraph(self):
         return mochy_get_hypergraph(self.h)

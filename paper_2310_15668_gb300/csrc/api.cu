@@ -443,6 +443,41 @@ int mochy_hyperedge_profile(mochy_ctx* ctx, int64_t* hp_h, int64_t* hp_3h) {
   return MOCHY_OK;
 }
 
+int mochy_star_node_profile(mochy_ctx* ctx, int64_t* np_h, int64_t* np_3h) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  MOCHY_TRY(device_guard(ctx));
+  if (!ctx->projected) return fail(MOCHY_E_NOT_PROJECTED, "call mochy_project first");
+  const int64_t N = ctx->n_nodes;
+  if (N == 0) return MOCHY_OK;
+  const size_t bytes = (size_t)N * 432 * 8;
+  void* d = nullptr;
+  MOCHY_TRY(dev_alloc(ctx, &d, bytes));
+  std::vector<unsigned long long> h((size_t)N * 432);
+  uint8_t t2h[432];
+  int rc = star_node_profiles(ctx, (unsigned long long*)d);
+  if (rc == MOCHY_OK &&
+      (cudaMemcpyAsync(h.data(), d, bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+       cudaMemcpyAsync(t2h, ctx->tables.t2h, 432, cudaMemcpyDeviceToHost, ctx->stream) !=
+           cudaSuccess ||
+       cudaStreamSynchronize(ctx->stream) != cudaSuccess))
+    rc = fail(MOCHY_E_CUDA, "profile copy failed");
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(ctx, d, bytes);
+  if (rc < 0) return rc;
+  for (int64_t v = 0; v < N; ++v) {
+    const unsigned long long* r = h.data() + (size_t)v * 432;
+    if (r[0] != 0ull) return fail(MOCHY_E_CUDA, "internal error: an instance mapped to no motif");
+    if (np_3h)
+      for (int t = 1; t <= MOCHY_N_3H; ++t) np_3h[v * MOCHY_N_3H + t - 1] = (int64_t)r[t];
+    if (np_h) {
+      int64_t* o = np_h + v * MOCHY_N_H;
+      for (int t = 0; t < MOCHY_N_H; ++t) o[t] = 0;
+      for (int t = 1; t <= MOCHY_N_3H; ++t) o[t2h[t] - 1] += (int64_t)r[t];
+    }
+  }
+  return MOCHY_OK;
+}
+
 int mochy_count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t seed,
                         int64_t* raw_h, int64_t* raw_3h, double* est_h, double* est_3h) {
   if (!ctx) return fail(MOCHY_E_INVALID, "null context");

@@ -190,6 +190,7 @@ int count_exact(mochy_ctx* ctx, const int32_t* d_anchors, int64_t n_anchors,
                 unsigned long long* d_hist);                          // count_exact.cu
 int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist);    // count_split.cu
 int hyperedge_profiles(mochy_ctx* ctx, unsigned long long* d_hp);    // count_exact.cu
+int star_node_profiles(mochy_ctx* ctx, unsigned long long* d_np);    // count_exact.cu
 int prepare_split(mochy_ctx* ctx);                                    // count_split.cu
 void release_split(mochy_ctx* ctx);                                   // count_split.cu
 int count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t seed,

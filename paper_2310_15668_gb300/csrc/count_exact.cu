@@ -215,6 +215,98 @@ k_hyperedge_profile(ExactArgs g, unsigned long long* __restrict__ hp) {
   }
 }
 
+// u in an ascending node list in global memory
+__device__ __forceinline__ bool in_sorted(const int32_t* __restrict__ s, int n, int32_t u) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int m = (lo + hi) >> 1;
+    if (s[m] < u) lo = m + 1; else hi = m;
+  }
+  return lo < n && s[lo] == u;
+}
+
+// Star node profiles (Section 3.1, "Node Profile (NP)" with star
+// ego-networks).  The star ego-network of v keeps the hyperedges that contain
+// v, so its instances are exactly the closed instances of G whose triple
+// intersection holds v: every closed instance (met once, from its smallest
+// member e_a, as in k_exact_rows) is added to the row of each node of
+// e_a & e_b & e_k.  np is n_nodes x 432 (index = 3h id).
+__global__ void __launch_bounds__(kExactThreads)
+k_star_profile(ExactArgs g, unsigned long long* __restrict__ np) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint16_t* lut = (uint16_t*)(smem + 432 * 8);
+  int32_t* anodes = (int32_t*)(lut + 2192);
+  uint32_t* codes = (uint32_t*)(anodes + 64);
+  __shared__ int64_t row_slot;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t code_words = (g.n_edges + 15) / 16;
+  for (int q = threadIdx.x; q < 2187; q += kExactThreads) lut[q] = g.lut3[q];
+  while (true) {
+    if (threadIdx.x == 0) row_slot = atomicAdd(g.queue, 1);
+    __syncthreads();
+    const int64_t slot = row_slot;
+    if (slot >= g.n_rows) break;
+    const int64_t a = g.rows[slot];
+    const int64_t ab = g.noff[a], ae = g.noff[a + 1];
+    const int A = (int)(g.eoff[a + 1] - g.eoff[a]);
+    if (threadIdx.x < A) anodes[threadIdx.x] = g.enode[g.eoff[a] + threadIdx.x];
+    for (int64_t q = threadIdx.x; q < code_words; q += kExactThreads) codes[q] = 0u;
+    __syncthreads();
+    for (int64_t p = ab + threadIdx.x; p < ae; p += kExactThreads) {
+      const uint2 e = g.nadj[p];
+      const uint32_t k = ent_id(e);
+      const uint32_t w = (uint32_t)min(entry_omega(e.y, A), 3);
+      atomicOr(&codes[k >> 4], w << (2 * (k & 15)));
+    }
+    __syncthreads();
+    for (int64_t idx = ab + warp; idx < ae; idx += kExactWarps) {
+      const uint2 eab = g.nadj[idx];
+      const uint32_t b = ent_id(eab);
+      if ((int64_t)b <= a) continue;                // closed instances: a < b < k
+      const int B = ent_size(eab);
+      const int x = entry_omega(eab.y, A);
+      const int64_t bb = g.noff[b], be = g.noff[b + 1];
+      const int64_t pa = warp_lower_bound(g.nadj, bb, be, (uint32_t)a);
+      const uint32_t mask_ba = g.nadj[pa].y;   // nodes of e_b lying in e_a
+      const int32_t* bnodes = g.enode + g.eoff[b];
+      for (int64_t q = pa + 1 + lane; q < be; q += 32) {
+        const uint2 ebk = g.nadj[q];
+        const uint32_t k = ent_id(ebk);
+        const int za = (int)((codes[k >> 4] >> (2 * (k & 15))) & 3u);
+        if (za == 0 || k <= b) continue;
+        const int C = ent_size(ebk);
+        const int y = entry_omega(ebk.y, B);
+        const int32_t* knodes = g.enode + g.eoff[k];
+        int z = za;
+        if (za == 3) z = sorted_overlap(anodes, A, knodes, C);
+        int t;
+        if (B <= kMaskedMax) {
+          t = __popc(mask_ba & ebk.y);
+        } else {
+          t = sorted_overlap3(anodes, A, bnodes, B, knodes, C);
+        }
+        if (t == 0) continue;                   // in no star ego-network
+        const int id = lut[ternary_code(A, B, C, x, y, z, t, g.theta)];
+        if (B <= kMaskedMax) {
+          uint32_t tm = mask_ba & ebk.y;        // positions in e_b of the common nodes
+          while (tm) {
+            const int pos = __ffs(tm) - 1;
+            tm &= tm - 1;
+            atomicAdd(&np[(int64_t)bnodes[pos] * 432 + id], 1ull);
+          }
+        } else {
+          for (int q2 = 0; q2 < A; ++q2) {
+            const int32_t u = anodes[q2];
+            if (in_sorted(bnodes, B, u) && in_sorted(knodes, C, u))
+              atomicAdd(&np[(int64_t)u * 432 + id], 1ull);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Test hook: the contribution of the outer-loop iterations of the given
 // anchors in Algorithm exact_motif_counting.  For anchor e_x, every pair
 // {p, q} of its neighbours with p < q is checked: counted when p and q are
@@ -311,6 +403,41 @@ int hyperedge_profiles(mochy_ctx* ctx, unsigned long long* d_hp) {
   per_sm = std::max(per_sm, 1);
   const unsigned grid = (unsigned)std::min<int64_t>((int64_t)ctx->num_sms * per_sm, E);
   k_hyperedge_profile<<<grid, kExactThreads, smem, st>>>(g, d_hp);
+  MOCHY_LAUNCHED();
+  return MOCHY_OK;
+}
+
+// The star node profiles of the projected hypergraph into d_np (n_nodes x
+// 432, cleared here).
+int star_node_profiles(mochy_ctx* ctx, unsigned long long* d_np) {
+  if (!ctx->projected) return fail(MOCHY_E_NOT_PROJECTED, "call mochy_project first");
+  cudaStream_t st = ctx->stream;
+  const int64_t E = ctx->n_edges;
+  MOCHY_CUDA(cudaMemsetAsync(d_np, 0, (size_t)std::max<int64_t>(ctx->n_nodes, 1) * 432 * 8, st));
+  if (E == 0) return MOCHY_OK;
+  MOCHY_CUDA(cudaMemsetAsync(ctx->counters, 0, 16 * sizeof(int32_t), st));
+  ExactArgs g;
+  g.n_edges = E;
+  g.eoff = ctx->eoff;
+  g.enode = ctx->enode;
+  g.noff = ctx->noff;
+  g.nadj = ctx->nadj;
+  g.rows = ctx->row_order;
+  g.n_rows = E;
+  g.queue = ctx->counters + 4;
+  g.lut3 = ctx->tables.lut3;
+  g.hist = nullptr;
+  g.theta = ctx->theta;
+  const size_t smem = exact_smem_bytes(E);
+  if (smem + 1024 > ctx->smem_optin)
+    return fail(MOCHY_E_UNSUPPORTED, "node profiles support at most 786432 hyperedges");
+  MOCHY_TRY(ensure_dynamic_smem((const void*)k_star_profile, smem));
+  int per_sm = 0;
+  MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_star_profile,
+                                                           kExactThreads, smem));
+  per_sm = std::max(per_sm, 1);
+  const unsigned grid = (unsigned)std::min<int64_t>((int64_t)ctx->num_sms * per_sm, E);
+  k_star_profile<<<grid, kExactThreads, smem, st>>>(g, d_np);
   MOCHY_LAUNCHED();
   return MOCHY_OK;
 }
