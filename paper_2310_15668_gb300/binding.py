@@ -477,6 +477,12 @@ class Server:
             load_library().mochy_server_destroy(self.h)
             self.h = None
 
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
     def __enter__(self):
         return self
 
