@@ -38,10 +38,18 @@
 //       are all zero is returned as zeros.
 //   R10 hyperedge ids are positions after duplicate removal (first
 //       occurrence kept, input order preserved).
+//   R11 in the variance theorems of MoCHy-A / MoCHy-A+, p_l[t] and q_n[t]
+//       count ordered pairs of distinct instances (the reading under which
+//       the stated formulas are the estimators' variances).
+//   R12 node profiles: the star ego-network of v keeps the hyperedges that
+//       contain v whole, and its instances are classified as in G.
 //
 // Parity pins: see tests/test_oracle_*.py (motif-table counts printed in the
 // paper, brute force over all triples, invariants, Philox known answers,
-// closed forms of the estimators and of the Chung-Lu expectations).
+// closed forms of the estimators and of the Chung-Lu expectations, the
+// per-anchor sampling bodies and the variance theorems, brute force of the
+// hyperedge and star node profiles).  The motif numbering's agreement with
+// the paper's lost figures (R1, R2) is unpinned: the tests compare patterns.
 
 #include <algorithm>
 #include <array>
