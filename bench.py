@@ -15,7 +15,9 @@ library's stream around K steps.  e2e: the same metric through mochy_load
 from pinned host buffers (host-to-device copy inside the timed region) and a
 device-to-host read of the counts.  roofline: the dominant kernel's duration
 is taken live from the library's traced CUDA events.  cpu_baseline: the
-single-threaded CPU oracle on a seeded anchor sample of the same hypergraph.
+CPU oracle (its anchor loop on every host core) on a seeded anchor sample of
+the same hypergraph.  sampled: candidates classified/s of MoCHy-A+ with
+r = 2,000,000 hyperwedges on the same projected hypergraph.
 
 batch (rank 0, one GPU): significance and CP of 16 seeded hypergraphs (E
 log-uniform in [2,000, 20,000], N = E/2, power-law sizes on [2, 25], Zipf(1.0)
@@ -54,15 +56,25 @@ METRIC = "hyperedge triples classified/s (exact)"
 UNIT = "triples/s"
 
 
+WORKLOADS = ("medium", "tiny", "zipf10k", "zipf40k")
+
+
 def _spec(workload: str, seed_offset: int):
+    """The bench workload (medium) or a smaller case of the same shape for
+    profilers (zipf10k, zipf40k: N = E/2, sizes s^-2.5 on [2, 25], Zipf(1.0)
+    members, seed 5)."""
     from paper_2310_15668_gb300 import synth
     import dataclasses
-    base = {"medium": synth.MEDIUM, "tiny": synth.TINY}[workload]
+    base = {"medium": synth.MEDIUM, "tiny": synth.TINY,
+            "zipf10k": synth.HypergraphSpec(5000, 10000, 2, 25, "powerlaw", 2.5, "zipf", 1.0,
+                                            seed=5),
+            "zipf40k": synth.HypergraphSpec(20000, 40000, 2, 25, "powerlaw", 2.5, "zipf", 1.0,
+                                            seed=5)}[workload]
     return dataclasses.replace(base, seed=base.seed + seed_offset)
 
 
 def _workload_name(spec) -> str:
-    return f"medium exact h/3h-motif counts: {spec.describe()}"
+    return f"exact h/3h-motif counts: {spec.describe()}"
 
 
 def _peaks():
@@ -147,9 +159,12 @@ def _dist():
     return ws, rank, local
 
 
-def _cpu_baseline(off, nodes, n_nodes, seconds: float, seed: int = 12345):
-    """Oracle (single thread) on a seeded anchor sample of the workload."""
+def _cpu_baseline(off, nodes, n_nodes, seconds: float, seed: int = 12345, threads: int = 0):
+    """The oracle's MoCHy-E (hash sets, the paper's hyperedge-centric loop)
+    on a seeded anchor sample of the workload, its anchor loop on `threads`
+    host threads (0 = every core this process may use)."""
     import oracle
+    nt = oracle.host_threads() if threads == 0 else threads
     E = off.size - 1
     deg_v = np.bincount(nodes, minlength=n_nodes).astype(np.int64)
     bound = np.add.reduceat(deg_v[nodes] - 1, off[:-1]) if E else np.zeros(0, np.int64)
@@ -158,24 +173,29 @@ def _cpu_baseline(off, nodes, n_nodes, seconds: float, seed: int = 12345):
     # anchors drawn uniformly (seeded), skipping hub-containing ones whose
     # neighbourhood bound exceeds 4,000 (one such anchor alone costs minutes)
     cap = 4_000
-    cand = [int(i) for i in order if bound[i] <= cap][:20000]
+    cand = [int(i) for i in order if bound[i] <= cap][:40000]
+    # every oracle call first builds its hash sets: timed once with no anchor
+    # and taken off each call's time
+    t = time.perf_counter()
+    oracle.count_exact_ranked(off, nodes, np.zeros(0, np.int32), None, threads=nt)
+    setup = time.perf_counter() - t
     done_inst, done_time, used, k = 0, 0.0, 0, 0
-    step = 1
+    step = nt
     while done_time < seconds and k < len(cand):
         anchors = np.array(cand[k:k + step], np.int32)
         k += step
         t = time.perf_counter()
-        h, _ = oracle.count_exact_subset(off, nodes, anchors)
-        dt = time.perf_counter() - t
+        h, _ = oracle.count_exact_ranked(off, nodes, anchors, None, threads=nt)
+        dt = max(time.perf_counter() - t - setup, 1e-6)
         done_inst += int(h.sum())
         done_time += dt
         used += anchors.size
-        step = min(step * 2, 512)
-    return {"value": done_inst / done_time if done_time > 0 else None, "unit": UNIT, "cores": 1,
+        step = min(step * 2, 1024 * nt)
+    return {"value": done_inst / done_time if done_time > 0 else None, "unit": UNIT, "cores": nt,
             "kind": "oracle",
             "sample": f"{used} anchors drawn uniformly by seed {seed} among hyperedges whose "
                       f"neighbourhood bound is at most {cap} ({done_inst} triples in "
-                      f"{done_time:.1f} s, oracle set-up excluded)"}
+                      f"{done_time:.1f} s on {nt} host threads, oracle set-up excluded)"}
 
 
 def run_reference(args):
@@ -202,12 +222,38 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": _workload_name(spec), "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                              "sample": r["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _sampled_measure(ctx, args):
+    """Candidates classified per second by MoCHy-A+ (Algorithm
+    "sampling_ver2") on the projected workload: r hyperwedges drawn with
+    Philox, every hyperedge adjacent to either end classified.  Device time
+    with CUDA events on the library's stream, after one warm-up call."""
+    import torch
+    from paper_2310_15668_gb300 import binding as B
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    r = int(args.sampled_r)
+    ctx.count_sampled(B.MOCHY_A_PLUS, r, 1)
+    times, cands = [], 0
+    for k in range(args.sampled_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        raw_h, _, _, _ = ctx.count_sampled(B.MOCHY_A_PLUS, r, 2 + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        cands = int(raw_h.sum())
+    ms = float(np.mean(times))
+    return {"metric": "candidates classified/s (MoCHy-A+)", "value": cands / (ms / 1000.0),
+            "unit": "candidates/s", "r": r, "candidates_per_call": cands, "ms_per_call": ms,
+            "calls": args.sampled_steps}
 
 
 def _batch_measure(args):
@@ -316,7 +362,7 @@ def run_gpu(args):
     off, nodes = synth.generate(spec)
     d_off = torch.from_numpy(off).cuda()
     d_nodes = torch.from_numpy(nodes).cuda()
-    ctx = B.Context(device=local)
+    ctx = B.Context(device=local, dense_threshold=args.dense_threshold)
     stream = torch.cuda.ExternalStream(ctx.stream, device=local)
     instances = 0
 
@@ -387,17 +433,29 @@ def run_gpu(args):
     st = stats_trace
     roof = None
     if dom == "dense triangles" and avg[dom] > 0:
-        # algorithmic bytes: every scanned word reads the three overlap planes
-        # of row a and of row b, the four size planes, and one bitmap word per
-        # heavy node of e_a & e_b (their mean number per hyperwedge is traced)
+        # algorithmic bytes of the classification (candidate stream, 5 B of
+        # HBM per classified candidate: a 4-byte hyperedge id and its 1-byte
+        # overlap); the candidates the dense kernel classifies per launch are
+        # its closed triangles, counted by the traced step
+        cand = float(st.get("candidates", 0))
+        sec = avg[dom] / 1000.0
+        achieved = 5.0 * cand / sec / 1e9
+        # the kernel's own loads: three overlap planes of rows a and b, four
+        # size planes and one bitmap word per heavy node of e_a & e_b per word
         words = float(st.get("words_scanned", 0))
         hw = float(st.get("dense_hyperwedges", 0)) or 1.0
         n_t = float(st.get("heavy_bitmaps", 0)) / hw
-        algo = words * 4.0 * (3 + 3 + 4 + n_t)
-        achieved = algo / (avg[dom] / 1000.0) / 1e9
+        loads = words * 4.0 * (3 + 3 + 4 + n_t)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_dense_triangles",
-                "kernel_ms": avg[dom], "peak_kind": peak_kind}
+                "frac": achieved / peak, "traffic": args.traffic_bytes,
+                "kernel": "k_dense_triangles", "kernel_ms": avg[dom], "peak_kind": peak_kind,
+                "candidates_per_launch": cand, "bytes_per_candidate": 5,
+                "l2_term": {"bytes_per_candidate": 15, "achieved_gbs": 15.0 * cand / sec / 1e9},
+                "load_model": {"bytes": loads, "achieved_gbs": loads / sec / 1e9,
+                               "frac": loads / sec / 1e9 / peak}}
+    sampled = None
+    if args.sampled_r > 0:
+        sampled = _sampled_measure(ctx, args)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = _cpu_baseline(off, nodes, spec.n_nodes, args.cpu_seconds)
@@ -413,7 +471,7 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (line graph of 30 GB per step)",
                        "parallelism": f"independent hypergraph per rank x{ws}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk.summary(), "phases_ms": avg, "trace": st,
+            "clocks": clk.summary(), "phases_ms": avg, "trace": st, "sampled": sampled,
             "batch": batch, "serving": serving}
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -426,7 +484,14 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["medium", "tiny"], default="medium")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="medium")
+    ap.add_argument("--dense-threshold", type=int, default=0,
+                    help="split kernel threshold (0: the tuner's choice)")
+    ap.add_argument("--traffic-bytes", type=float, default=None,
+                    help="DRAM bytes per dense-kernel launch from an ncu capture, if known")
+    ap.add_argument("--sampled-r", type=int, default=2_000_000,
+                    help="MoCHy-A+ samples of the candidates/s line (0: skip)")
+    ap.add_argument("--sampled-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-seconds", type=float, default=10.0)

@@ -15,8 +15,10 @@
  *
  * Limits: at most 2^26 - 1 hyperedges, 2^31 - 1 nodes, 63 nodes per
  * hyperedge; the per-hyperwedge scan kernel (exact_kernel = 1) needs at most
- * 786,432 hyperedges (it stages a row's adjacency in shared memory).  A call
- * outside these limits returns MOCHY_E_UNSUPPORTED.
+ * 786,432 hyperedges (it stages a row's adjacency in shared memory); the
+ * split kernel keeps at most 2,096,128 rows of one hypergraph dense (the
+ * tuner never picks more; a forced dense_threshold that makes more fails).
+ * A call outside these limits returns MOCHY_E_UNSUPPORTED.
  *
  * Motif ids: h-motifs are numbered 1..26, 3h-motifs 1..431 (arrays are
  * indexed id-1).  The paper's figures that fix the numbering are lost; the
@@ -132,6 +134,21 @@ int mochy_count_exact_subset(mochy_ctx* ctx, const int32_t* h_anchors,
                              int64_t n_anchors, int64_t out_h[MOCHY_N_H],
                              int64_t out_3h[MOCHY_N_3H]);
 
+/* The part of the exact count that the split kernel (exact_kernel = 0)
+ * adds for the rows h_rows[0..n_rows) (host int32 hyperedge ids; an id may
+ * not repeat): open instances centred at a listed row, plus closed
+ * instances whose first member in the split kernel's row order is listed.
+ * That order puts the rows of line degree below the dense threshold T
+ * first, ascending by id, then the rows of line degree >= T ascending by
+ * (line degree, id); T is cfg.dense_threshold when set, else the tuner's
+ * choice (mochy_trace_read reports it).  This is Algorithm
+ * "exact_motif_counting" (Section 3.2) with its id comparison i < min(j, k)
+ * replaced by that order; any fixed total order counts every instance once,
+ * so summed over all rows it equals mochy_count_exact.  Needs mochy_project;
+ * MOCHY_E_INVALID for the scan kernel or a batch. */
+int mochy_count_exact_rows(mochy_ctx* ctx, const int32_t* h_rows, int64_t n_rows,
+                           int64_t out_h[MOCHY_N_H], int64_t out_3h[MOCHY_N_3H]);
+
 /* Hyperedge profiles (Section 3.1, "Hyperedge Profile (HP)"; Section 4.1
  * for their 3h-motif form): hp_h[e * 26 + t - 1] is the number of instances
  * of h-motif t that include hyperedge e, hp_3h[e * 431 + t - 1] the same for
@@ -177,7 +194,8 @@ int mochy_count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t se
  * until the process exits), so MOCHY_A takes at most 65,536 samples per call
  * (more returns MOCHY_E_UNSUPPORTED); MOCHY_A_PLUS has no limit.  The first
  * call on a device looks the array up (cudaGetSymbolAddress) and should come
- * before any stream capture.  All calls share the array: calls whose GPU work
+ * before any stream capture; the address is kept for the process, so the
+ * call must not be used on a device after cudaDeviceReset.  All calls share the array: calls whose GPU work
  * overlaps race, so run them one after another on the context's stream.
  * MOCHY_A waits for its stream once (to size its work); the outputs are
  * ready when the context's stream (mochy_stream) has completed. */

@@ -1,7 +1,9 @@
 """Reference oracle for MoCHy motif counting (TEST INFRASTRUCTURE ONLY).
 
-A plain, slow, single-threaded C++ restatement of the paper's algorithms
-(``mochy_oracle.cpp``), loaded with ctypes.  Only the test suite, the smoke
+A plain, slow C++ restatement of the paper's algorithms
+(``mochy_oracle.cpp``), loaded with ctypes; one thread, except the anchor
+loop of ``count_exact_ranked`` and ``line_degrees`` (host threads, the
+paper's parallel scheme).  Only the test suite, the smoke
 check and the bench's CPU-baseline leg may import this package; the CUDA
 library never does, and this package never imports the library.
 
@@ -9,7 +11,7 @@ Functions whose parity is pinned by tests/test_oracle_*.py:
   tables, count_kh           motif tables and the kh-motif chain
   philox                     Philox4x32-10 known answers
   dedupe, project            load and line-graph construction
-  count_exact, count_exact_subset
+  count_exact, count_exact_subset, count_exact_ranked, line_degrees
   count_sampled              MoCHy-A / MoCHy-A+
   randomize, profile         Chung-Lu null model, significance, CP
 """
@@ -34,16 +36,28 @@ A, A_PLUS = 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with the host compiler (plain -O2, one thread)."""
+    """Compile the oracle with the host compiler (plain -O2; OpenMP for the
+    anchor loops when the compiler has it, else one thread)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC",
-                           "-o", tmp, _SRC])
+    base = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC]
+    try:
+        subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(base)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def host_threads() -> int:
+    """Host cores this process may use."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def _load():
@@ -172,6 +186,47 @@ def count_exact_subset(offsets, nodes, anchors, theta: int = 1):
         _p(anc if anc.size else np.zeros(1, np.int32)), ctypes.c_int64(anc.size),
         _p(h), _p(h3)), "count_exact_subset")
     return h, h3
+
+
+def count_exact_ranked(offsets, nodes, anchors, rank=None, theta: int = 1,
+                       threads: int = 1):
+    """MoCHy-E restricted to the outer-loop iterations of ``anchors`` with the
+    hyperedges compared by ``rank`` (int64 per hyperedge after duplicate
+    removal; ``None`` compares ids, as Algorithm "exact_motif_counting"
+    does): open instances centred at an anchor plus closed instances whose
+    lowest-ranked member is an anchor.  ``threads`` host threads (0 = all)."""
+    off, nod = _csr(offsets, nodes)
+    anc = np.ascontiguousarray(anchors, dtype=np.int32)
+    rk = None if rank is None else np.ascontiguousarray(rank, dtype=np.int64)
+    h = np.zeros(N_H, np.int64)
+    h3 = np.zeros(N_3H, np.int64)
+    nt = host_threads() if threads == 0 else int(threads)
+    _check(_load().orc_count_exact_ranked(
+        ctypes.c_int64(off.size - 1), _p(off), _p(nod), ctypes.c_int32(theta),
+        _p(anc if anc.size else np.zeros(1, np.int32)), ctypes.c_int64(anc.size),
+        None if rk is None else _p(rk), ctypes.c_int32(nt), _p(h), _p(h3)),
+        "count_exact_ranked")
+    return h, h3
+
+
+def count_exact_threads(offsets, nodes, theta: int = 1, threads: int = 0):
+    """The full MoCHy-E count with every hyperedge an anchor, on ``threads``
+    host threads (0 = all), neighbourhoods computed on the fly."""
+    n_kept = dedupe(offsets, nodes)[0].size - 1
+    return count_exact_ranked(offsets, nodes, np.arange(n_kept, dtype=np.int32), None,
+                              theta, threads)
+
+
+def line_degrees(offsets, nodes, threads: int = 0):
+    """|N_e| of every hyperedge (after duplicate removal), from the incidence
+    lists, without building the line graph."""
+    off, nod = _csr(offsets, nodes)
+    n_kept = dedupe(off, nod)[0].size - 1
+    deg = np.zeros(max(n_kept, 1), np.int64)
+    nt = host_threads() if threads == 0 else int(threads)
+    _check(_load().orc_line_degrees(ctypes.c_int64(off.size - 1), _p(off), _p(nod),
+                                    ctypes.c_int32(nt), _p(deg)), "line_degrees")
+    return deg[:n_kept]
 
 
 def count_sampled(offsets, nodes, method: int, samples: int, seed: int, theta: int = 1):

@@ -1,11 +1,14 @@
 // Reference oracle for MoCHy h-motif / 3h-motif counting.
 //
-// TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, single-threaded CPU
-// restatement of the paper's definitions and algorithms ("Hypergraph motifs
-// and their extensions beyond binary", arXiv 2310.15668).  Only the test
-// suite, the smoke check and the bench's CPU-baseline leg may load it.  It
-// shares no code, header, table or constant generator with the CUDA library;
-// the two are checked against each other.
+// TEST INFRASTRUCTURE ONLY.  This file is a plain, slow CPU restatement of
+// the paper's definitions and algorithms ("Hypergraph motifs and their
+// extensions beyond binary", arXiv 2310.15668).  Only the test suite, the
+// smoke check and the bench's CPU-baseline leg may load it.  It shares no
+// code, header, table or constant generator with the CUDA library; the two
+// are checked against each other.  Everything runs on one thread except the
+// anchor loop of orc_count_exact_ranked and orc_line_degrees, which may
+// share their outer loop among host threads (the paper's own parallel
+// scheme, each thread with its own histogram).
 //
 // Every function cites the passage it follows.  Hash containers are the
 // standard library's, as in the paper's own implementation (Section 5.1).
@@ -61,6 +64,10 @@
 #include <unordered_map>
 #include <unordered_set>
 #include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -676,18 +683,31 @@ int orc_star_node_profile(int64_t n_nodes, int64_t n_edges, const int64_t* off,
   return 0;
 }
 
-// MoCHy-E restricted to the outer-loop hyperedges in `anchors`; the line
-// graph rows of the anchors come from the on-the-fly neighbour routine
+// MoCHy-E restricted to the outer-loop hyperedges in `anchors`, with the
+// hyperedges compared by `rank` (Algorithm "exact_motif_counting" compares
+// ids, i < min(j, k); any fixed total order counts every instance exactly
+// once, at its centre when open and at its first member when closed).  The
+// line-graph rows of the anchors come from the on-the-fly neighbour routine
 // (Appendix "on-the-fly", getNeighbors) and the overlaps of neighbour pairs
-// from set intersection, so large graphs need not be projected whole.
-int orc_count_exact_subset(int64_t n_edges, const int64_t* off,
-                           const int32_t* nodes, int32_t theta,
-                           const int32_t* anchors, int64_t n_anchors,
-                           int64_t* out_h, int64_t* out_3h) {
+// from set intersection, so large hypergraphs need not be projected whole.
+// With threads > 1 the anchors are shared out among host threads, each with
+// its own histogram, summed once at the end (the paper's parallel scheme,
+// Section "Parallel and On-the-fly Implementations").
+int orc_count_exact_ranked(int64_t n_edges, const int64_t* off, const int32_t* nodes,
+                           int32_t theta, const int32_t* anchors, int64_t n_anchors,
+                           const int64_t* rank, int32_t threads, int64_t* out_h,
+                           int64_t* out_3h) {
   Hypergraph G;
   if (build(n_edges, off, nodes, G)) return -1;
   std::fill(out_h, out_h + 26, 0);
   std::fill(out_3h, out_3h + 431, 0);
+  const int64_t E = (int64_t)G.e.size();
+  for (int64_t a = 0; a < n_anchors; ++a)
+    if (anchors[a] < 0 || anchors[a] >= E) return -1;
+  // rank of hyperedge x; the id itself when no order is given
+  auto before = [&](int64_t x, int64_t y) {
+    return rank ? rank[x] < rank[y] : x < y;
+  };
   auto overlap = [&](int64_t x, int64_t y) {
     const auto& s = G.e[x].size() <= G.e[y].size() ? G.e[x] : G.e[y];
     const auto& o = G.e[x].size() <= G.e[y].size() ? G.eset[y] : G.eset[x];
@@ -695,10 +715,9 @@ int orc_count_exact_subset(int64_t n_edges, const int64_t* off,
     for (int32_t v : s) c += o.count(v) ? 1 : 0;
     return c;
   };
-  for (int64_t a = 0; a < n_anchors; ++a) {
-    const int32_t i = anchors[a];
-    if (i < 0 || i >= (int64_t)G.e.size()) return -1;
-    std::map<int32_t, int32_t> Ni;   // getNeighbors(e_i)
+  // the body of the outer loop for one anchor e_i, into h / h3
+  auto anchor_body = [&](int32_t i, int64_t* h, int64_t* h3) {
+    std::map<int32_t, int32_t> Ni;   // getNeighbors(e_i): e_j -> omega(i, j)
     for (int32_t v : G.e[i])
       for (int32_t j : G.ev.at(v))
         if (j != i) Ni[j] += 1;
@@ -707,13 +726,73 @@ int orc_count_exact_subset(int64_t n_edges, const int64_t* off,
       for (size_t y = x + 1; y < N.size(); ++y) {
         const int32_t j = N[x].first, k = N[y].first;
         const int64_t wjk = overlap(j, k);
-        if (!(wjk == 0 || i < std::min(j, k))) continue;
+        if (!(wjk == 0 || (before(i, j) && before(i, k)))) continue;
         auto r = regions(G, i, j, k, N[x].second, wjk, N[y].second);
-        int h, h3;
-        classify(r, theta, &h, &h3);
-        out_h[h - 1] += 1;
-        out_3h[h3 - 1] += 1;
+        int hh, t3;
+        classify(r, theta, &hh, &t3);
+        h[hh - 1] += 1;
+        h3[t3 - 1] += 1;
       }
+  };
+  tables();   // built once, before any thread reads it
+  const int nt = threads > 1 ? threads : 1;
+  std::vector<std::vector<int64_t>> part(nt, std::vector<int64_t>(26 + 431, 0));
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1)
+#endif
+  for (int64_t a = 0; a < n_anchors; ++a) {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    anchor_body(anchors[a], part[tid].data(), part[tid].data() + 26);
+  }
+  for (int t = 0; t < nt; ++t) {
+    for (int q = 0; q < 26; ++q) out_h[q] += part[t][q];
+    for (int q = 0; q < 431; ++q) out_3h[q] += part[t][26 + q];
+  }
+  return 0;
+}
+
+// MoCHy-E restricted to the outer-loop hyperedges in `anchors` (ids
+// compared as in Algorithm "exact_motif_counting"), one thread.
+int orc_count_exact_subset(int64_t n_edges, const int64_t* off,
+                           const int32_t* nodes, int32_t theta,
+                           const int32_t* anchors, int64_t n_anchors,
+                           int64_t* out_h, int64_t* out_3h) {
+  return orc_count_exact_ranked(n_edges, off, nodes, theta, anchors, n_anchors, nullptr, 1,
+                                out_h, out_3h);
+}
+
+// Line-graph degree |N_{e_i}| of every hyperedge (Section 2.1 "Line Graph":
+// the hyperedges other than e_i that share a node with it), from the
+// incidence lists: |(union of E_v over v in e_i) \ {e_i}|, each hyperedge
+// counted once by marking it with the current i.
+int orc_line_degrees(int64_t n_edges, const int64_t* off, const int32_t* nodes,
+                     int32_t threads, int64_t* degrees) {
+  Hypergraph G;
+  if (build(n_edges, off, nodes, G)) return -1;
+  const int64_t E = (int64_t)G.e.size();
+  const int nt = threads > 1 ? threads : 1;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+  {
+    std::vector<int64_t> mark(E, -1);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+    for (int64_t i = 0; i < E; ++i) {
+      int64_t d = 0;
+      mark[i] = i;
+      for (int32_t v : G.e[i])
+        for (int32_t j : G.ev.at(v))
+          if (mark[j] != i) {
+            mark[j] = i;
+            ++d;
+          }
+      degrees[i] = d;
+    }
   }
   return 0;
 }

@@ -26,7 +26,7 @@ E_INVALID, E_NOMEM, E_CUDA, E_TIMEOUT, E_NOT_PROJECTED, E_UNSUPPORTED, E_BUSY = 
 EXPORTS = [
     "mochy_config_default", "mochy_create", "mochy_destroy", "mochy_load", "mochy_load_device",
     "mochy_get_hypergraph", "mochy_project", "mochy_line_degrees", "mochy_count_exact",
-    "mochy_count_exact_subset", "mochy_count_sampled", "mochy_randomize", "mochy_profile",
+    "mochy_count_exact_subset", "mochy_count_exact_rows", "mochy_count_sampled", "mochy_randomize", "mochy_profile",
     "mochy_motif_pattern", "mochy_stream", "mochy_device_bytes", "mochy_kernel_launches",
     "mochy_strerror", "mochy_last_error", "mochy_trace", "mochy_trace_read",
     "mochy_count_sampled_noalloc", "mochy_profile_batch", "mochy_server_create",
@@ -133,6 +133,7 @@ def load_library(path: str = LIB_PATH):
             lib.mochy_line_degrees.argtypes = [vp, vp]
             lib.mochy_count_exact.argtypes = [vp, vp, vp]
             lib.mochy_count_exact_subset.argtypes = [vp, vp, i64, vp, vp]
+            lib.mochy_count_exact_rows.argtypes = [vp, vp, i64, vp, vp]
             lib.mochy_count_sampled.argtypes = [vp, ctypes.c_int, i64, ctypes.c_uint64, vp, vp,
                                                 vp, vp]
             lib.mochy_randomize.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint32,
@@ -243,6 +244,16 @@ def mochy_count_exact_subset(ctx: int, anchors) -> tuple:
     _check(load_library().mochy_count_exact_subset(ctx, _p(a if a.size else np.zeros(1, np.int32)),
                                                    a.size, _p(h), _p(h3)),
            "mochy_count_exact_subset")
+    return h, h3
+
+
+def mochy_count_exact_rows(ctx: int, rows) -> tuple:
+    a = np.ascontiguousarray(rows, dtype=np.int32)
+    h = np.zeros(N_H, np.int64)
+    h3 = np.zeros(N_3H, np.int64)
+    _check(load_library().mochy_count_exact_rows(ctx, _p(a if a.size else np.zeros(1, np.int32)),
+                                                 a.size, _p(h), _p(h3)),
+           "mochy_count_exact_rows")
     return h, h3
 
 
@@ -406,6 +417,9 @@ class Context:
 
     def count_exact_subset(self, anchors):
         return mochy_count_exact_subset(self.h, anchors)
+
+    def count_exact_rows(self, rows):
+        return mochy_count_exact_rows(self.h, rows)
 
     def count_sampled(self, method, samples, seed):
         return mochy_count_sampled(self.h, method, samples, seed)

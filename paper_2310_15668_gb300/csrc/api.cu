@@ -408,6 +408,34 @@ int mochy_count_exact_subset(mochy_ctx* ctx, const int32_t* h_anchors, int64_t n
   return rc;
 }
 
+int mochy_count_exact_rows(mochy_ctx* ctx, const int32_t* h_rows, int64_t n, int64_t* out_h,
+                           int64_t* out_3h) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  if (n < 0 || (n > 0 && !h_rows)) return fail(MOCHY_E_INVALID, "bad rows");
+  if (!ctx->projected) return fail(MOCHY_E_NOT_PROJECTED, "call mochy_project first");
+  if (ctx->exact_kernel != 0) return fail(MOCHY_E_INVALID, "row subsets need the split kernel");
+  MOCHY_TRY(device_guard(ctx));
+  std::vector<char> seen((size_t)ctx->n_edges, 0);
+  for (int64_t a = 0; a < n; ++a) {
+    if (h_rows[a] < 0 || h_rows[a] >= ctx->n_edges)
+      return fail(MOCHY_E_INVALID, "row out of range");
+    if (seen[(size_t)h_rows[a]]) return fail(MOCHY_E_INVALID, "repeated row");
+    seen[(size_t)h_rows[a]] = 1;
+  }
+  void* d = nullptr;
+  MOCHY_TRY(dev_alloc(ctx, &d, (size_t)std::max<int64_t>(n, 1) * 4));
+  int rc = MOCHY_OK;
+  if (n > 0 && cudaMemcpyAsync(d, h_rows, (size_t)n * 4, cudaMemcpyHostToDevice,
+                               ctx->stream) != cudaSuccess) {
+    rc = fail(MOCHY_E_CUDA, "row copy failed");
+  }
+  if (rc == MOCHY_OK) rc = count_split_rows(ctx, (const int32_t*)d, n, ctx->hist);
+  if (rc == MOCHY_OK) rc = fetch_counts(ctx, out_h, out_3h);
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(ctx, d, (size_t)std::max<int64_t>(n, 1) * 4);
+  return rc;
+}
+
 int mochy_hyperedge_profile(mochy_ctx* ctx, int64_t* hp_h, int64_t* hp_3h) {
   if (!ctx) return fail(MOCHY_E_INVALID, "null context");
   MOCHY_TRY(device_guard(ctx));
@@ -620,10 +648,11 @@ int mochy_trace_read(mochy_ctx* ctx, char* buf, int64_t len) {
            "\"clk_setup\": %llu, \"clk_words\": %llu, \"clk_finish\": %llu, "
            "\"clk_groups\": %llu, \"clk_light\": %llu, \"clk_sort\": %llu, "
            "\"light_entries\": %llu, \"dense_hyperwedges\": %llu, \"light_nodes\": %llu, "
-           "\"heavy_bitmaps\": %llu}",
+           "\"heavy_bitmaps\": %llu, \"slots_evicted\": %llu, \"slots_flushed_full\": %llu, "
+           "\"dense_rows_counted\": %llu}",
            (long long)ctx->n_dense, ctx->dense_thr_used, (long long)ctx->wwords,
            (long long)ctx->n_heavy, st[0], st[1], st[2], st[3], st[4], st[5], st[6], st[7], st[8],
-           st[9], st[10], st[11], st[12], st[13], st[14]);
+           st[9], st[10], st[11], st[12], st[13], st[14], st[16], st[17], st[18]);
   js += tail;
   if ((int64_t)js.size() + 1 > len) return fail(MOCHY_E_INVALID, "buffer too small");
   memcpy(buf, js.c_str(), js.size() + 1);

@@ -49,6 +49,12 @@ constexpr uint32_t kIdBits = 26;
 constexpr uint32_t kIdMask = (1u << kIdBits) - 1u;
 constexpr int kMaskedMax = 32;
 
+// Widest window of dense words the dense-triangle kernel accepts: each lane
+// counts its share of a hyperwedge's candidates (at most 32 per word, one
+// word in 32 of the window) into 16-bit halves of its bins, which stay below
+// 65,536 while the window has at most 65,504 words.
+constexpr int64_t kMaxWindowWords = 65504;
+
 __host__ __device__ inline uint32_t ent_id(uint2 e) { return e.x & kIdMask; }
 __host__ __device__ inline int ent_size(uint2 e) { return (int)(e.x >> kIdBits); }
 
@@ -160,7 +166,7 @@ struct mochy_ctx {
   char phase_name[8][24];
   double phase_ms[8];
   unsigned long long* stats = nullptr;   // [8] device counters, when tracing
-  unsigned long long last_stats[16];
+  unsigned long long last_stats[24];
 };
 
 namespace mochy {
@@ -189,6 +195,8 @@ int project_graph(mochy_ctx* ctx);                                    // project
 int count_exact(mochy_ctx* ctx, const int32_t* d_anchors, int64_t n_anchors,
                 unsigned long long* d_hist);                          // count_exact.cu
 int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist);    // count_split.cu
+int count_split_rows(mochy_ctx* ctx, const int32_t* d_rows, int64_t n_rows,
+                     unsigned long long* d_hist);                     // count_split.cu
 int hyperedge_profiles(mochy_ctx* ctx, unsigned long long* d_hp);    // count_exact.cu
 int star_node_profiles(mochy_ctx* ctx, unsigned long long* d_np);    // count_exact.cu
 int prepare_split(mochy_ctx* ctx);                                    // count_split.cu

@@ -40,8 +40,9 @@ constexpr int kOpenWarps = kOpenThreads / 32;
 constexpr int kTable = 256;   // per-warp class table of the open-pair kernel
 constexpr int kClasses = 5;   // size classes of a simple closed candidate
 // tracing counters: [0..7] totals and cycles, [8..71] rest combinations,
-// [72..79] setup sections and sizes
-constexpr int kStatWords = 80;
+// [72..79] setup sections and sizes, [80] signature slots evicted, [81]
+// slots flushed full, [82] dense rows counted
+constexpr int kStatWords = 88;
 
 // Size class of |e_k| for a closed candidate with both overlaps 1: its motif
 // and its three "as if open" terms depend on |e_k| only through the states
@@ -111,6 +112,9 @@ struct SplitArgs {
   const int32_t* order;
   int64_t n_order;
   int32_t* queue;
+  // open pairs: only these centres when non-null (a subset of the rows)
+  const int32_t* centres;
+  int64_t n_centres;
   // batch of disjoint hypergraphs: hist holds n_units histograms of 432
   int32_t n_units;
   const int64_t* nseg;       // [n_units+1] node ranges
@@ -247,8 +251,9 @@ __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
   int32_t* cnt = tcnt[warp];
   const int64_t nw = (int64_t)gridDim.x * kOpenWarps;
   if (!kSeg) {
-    for (int64_t c = (int64_t)blockIdx.x * kOpenWarps + warp; c < g.n_edges; c += nw)
-      open_centre(g, c, hist, lut, key, cnt);
+    const int64_t nc = g.centres ? g.n_centres : g.n_edges;
+    for (int64_t q = (int64_t)blockIdx.x * kOpenWarps + warp; q < nc; q += nw)
+      open_centre(g, g.centres ? (int64_t)g.centres[q] : q, hist, lut, key, cnt);
     __syncthreads();
     flush_hist(g.hist, hist);
     return;
@@ -469,6 +474,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
     const int64_t rb = g.noff[a], re = g.noff[a + 1];
     const int A = (int)(g.eoff[a + 1] - g.eoff[a]);
     if (threadIdx.x < A) anodes[threadIdx.x] = g.enode[g.eoff[a] + threadIdx.x];
+    if (g.stats && threadIdx.x == 0) atomicAdd(&g.stats[82], 1ull);
     // omega planes of row a (bits 0, 1, 2 of min(omega, 7)), indexed by word - WLO
     const uint32_t* AR = g.dbits + dboff + (int64_t)(ad - dbase) * 3 * WN;
     if (threadIdx.x == 0) row_next = rb;
@@ -798,6 +804,7 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
             q = me.snext;
             __syncwarp();
             if (lane == 0) me.snext = (q + 1) % kSlots;
+            if (g.stats && lane == 0) atomicAdd(&g.stats[80], 1ull);
             flush_slot(me, q, hist, lut, A);
           }
           if (lane == 0) {
@@ -811,7 +818,10 @@ __global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
         __syncwarp();
         if (lane == 0) me.sn[q] = nq;
         __syncwarp();
-        if (nq >= kSlotFlush) flush_slot(me, q, hist, lut, A);
+        if (nq >= kSlotFlush) {
+          if (g.stats && lane == 0) atomicAdd(&g.stats[81], 1ull);
+          flush_slot(me, q, hist, lut, A);
+        }
       } else {
 #pragma unroll
         for (int c = 0; c < 2 * kClasses; ++c) {
@@ -1334,6 +1344,13 @@ int prepare_split(mochy_ctx* ctx) {
     release_split(ctx);
     return fail(MOCHY_E_UNSUPPORTED, "too many dense rows for the shared-memory bitmap");
   }
+  if (wmax > kMaxWindowWords) {
+    // a lane of the dense kernel adds up to 32 per word of its share of the
+    // window into 16-bit halves of its bins
+    release_split(ctx);
+    return fail(MOCHY_E_UNSUPPORTED, "more than " + std::to_string(kMaxWindowWords * 32) +
+                                         " dense rows in one hypergraph; raise dense_threshold");
+  }
   const size_t b_dbits = al((size_t)std::max<int64_t>(dwords, 1) * 4);
   const size_t rest = b_dbits + b_hidx + b_sbits + 2 * b_ord + b_dsize;
   void* p1;
@@ -1498,6 +1515,8 @@ struct PhaseTimer {
       cudaMemcpy(c->last_stats, c->stats, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
       cudaMemcpy(c->last_stats + 8, c->stats + 72, 8 * sizeof(unsigned long long),
                  cudaMemcpyDeviceToHost);
+      cudaMemcpy(c->last_stats + 16, c->stats + 80, 8 * sizeof(unsigned long long),
+                 cudaMemcpyDeviceToHost);
     }
     if (stats && print) {
       unsigned long long combo[64];
@@ -1588,6 +1607,8 @@ static int plan_split(mochy_ctx* ctx, unsigned long long* d_hist, bool stats, Sp
   g.order = nullptr;
   g.n_order = 0;
   g.queue = nullptr;
+  g.centres = nullptr;
+  g.n_centres = 0;
   g.n_units = ctx->n_units;
   g.nseg = ctx->d_nseg;
   g.seg = ctx->d_seg;
@@ -1597,29 +1618,51 @@ static int plan_split(mochy_ctx* ctx, unsigned long long* d_hist, bool stats, Sp
   return ctx->n_units > 1 ? plan_kernels<true>(ctx, p) : plan_kernels<false>(ctx, p);
 }
 
+// Rows the counting kernels work on: every centre and the split's sparse and
+// dense work orders, or a subset of the rows.
+struct WorkLists {
+  const int32_t* centres = nullptr;   // null: every row is a centre
+  int64_t n_centres = 0;
+  const int32_t* sparse = nullptr;
+  int64_t n_sparse = 0;
+  const int32_t* dense = nullptr;
+  int64_t n_dense = 0;
+};
+
+static WorkLists all_rows(const mochy_ctx* ctx) {
+  WorkLists w;
+  w.sparse = ctx->sparse_order;
+  w.n_sparse = ctx->n_sparse;
+  w.dense = ctx->dense_order;
+  w.n_dense = ctx->n_dense;
+  return w;
+}
+
 // The counting kernels: open pairs, triangles from sparse rows, triangles of
 // dense rows.  Stream operations only (capturable).
 template <bool kSeg>
-static int launch_split(mochy_ctx* ctx, SplitPlan p, PhaseTimer* timer) {
+static int launch_split(mochy_ctx* ctx, SplitPlan p, PhaseTimer* timer, const WorkLists& wl) {
   cudaStream_t st = ctx->stream;
   SplitArgs g = p.g;
   MOCHY_CUDA(cudaMemsetAsync(ctx->counters, 0, 16 * sizeof(int32_t), st));
-  if (p.grid_open > 0) {
+  g.centres = wl.centres;
+  g.n_centres = wl.n_centres;
+  if (p.grid_open > 0 && (!wl.centres || wl.n_centres > 0)) {
     k_open_pairs<kSeg><<<p.grid_open, kOpenThreads, 0, st>>>(g);
     MOCHY_LAUNCHED();
   }
   if (timer) timer->mark("open pairs");
-  if (p.grid_sparse > 0) {
-    g.order = ctx->sparse_order;
-    g.n_order = ctx->n_sparse;
+  if (p.grid_sparse > 0 && wl.n_sparse > 0) {
+    g.order = wl.sparse;
+    g.n_order = wl.n_sparse;
     g.queue = ctx->counters + 5;
     k_sparse_triangles<kSeg><<<p.grid_sparse, kThreads, p.smem_sparse, st>>>(g, p.max_deg);
     MOCHY_LAUNCHED();
     if (timer) timer->mark("sparse triangles");
   }
-  if (p.grid_dense > 0) {
-    g.order = ctx->dense_order;
-    g.n_order = ctx->n_dense;
+  if (p.grid_dense > 0 && wl.n_dense > 0) {
+    g.order = wl.dense;
+    g.n_order = wl.n_dense;
     g.queue = ctx->counters + 6;
     auto kern = ctx->theta == 1 ? k_dense_triangles<true, kSeg> : k_dense_triangles<false, kSeg>;
     kern<<<p.grid_dense, kDThreads, p.smem_dense, st>>>(g);
@@ -1645,10 +1688,71 @@ int count_exact_split(mochy_ctx* ctx, unsigned long long* d_hist) {
   SplitPlan plan;
   MOCHY_TRY(plan_split(ctx, d_hist, timer.stats, &plan));
   if (ctx->n_units > 1) {
-    MOCHY_TRY(launch_split<true>(ctx, plan, &timer));
+    MOCHY_TRY(launch_split<true>(ctx, plan, &timer, all_rows(ctx)));
   } else {
-    MOCHY_TRY(launch_split<false>(ctx, plan, &timer));
+    MOCHY_TRY(launch_split<false>(ctx, plan, &timer, all_rows(ctx)));
   }
+  timer.report(ctx);
+  return MOCHY_OK;
+}
+
+namespace {
+// rows of a subset split by kind: sparse rows to the front of `sparse`,
+// dense rows to the front of `dense` (in any order), counts in cnt[0..1]
+__global__ void k_rows_by_kind(int64_t n, const int32_t* __restrict__ rows,
+                               const int32_t* __restrict__ didx, int32_t* __restrict__ sparse,
+                               int32_t* __restrict__ dense, unsigned long long* __restrict__ cnt) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int32_t r = rows[q];
+  if (didx[r] >= 0) dense[atomicAdd(&cnt[1], 1ull)] = r;
+  else sparse[atomicAdd(&cnt[0], 1ull)] = r;
+}
+}  // namespace
+
+// The part of the split count that a set of rows contributes: open instances
+// centred at a row of the set, and closed instances whose first member in
+// the split's order (sparse rows by id, then dense rows by line degree and
+// id) is in the set.  Summed over all rows it is the exact count.
+int count_split_rows(mochy_ctx* ctx, const int32_t* d_rows, int64_t n_rows,
+                     unsigned long long* d_hist) {
+  if (ctx->n_units != 1) return fail(MOCHY_E_INVALID, "row subsets need a lone hypergraph");
+  cudaStream_t st = ctx->stream;
+  PhaseTimer timer(ctx);
+  if (timer.stats && !ctx->stats) {
+    void* p;
+    MOCHY_TRY(dev_alloc(ctx, &p, kStatWords * sizeof(unsigned long long)));
+    ctx->stats = (unsigned long long*)p;
+  }
+  if (timer.stats)
+    MOCHY_CUDA(cudaMemsetAsync(ctx->stats, 0, kStatWords * sizeof(unsigned long long), st));
+  MOCHY_CUDA(cudaMemsetAsync(d_hist, 0, 432 * 8, st));
+  timer.mark("start");
+  MOCHY_TRY(prepare_split(ctx));
+  timer.mark("prepare");
+  if (n_rows == 0) return MOCHY_OK;
+  void* t;
+  MOCHY_TRY(scratch(ctx, 3, (size_t)n_rows * 8 + 64, &t));
+  unsigned long long* cnt = (unsigned long long*)t;
+  int32_t* sparse = (int32_t*)((char*)t + 64);
+  int32_t* dense = sparse + n_rows;
+  MOCHY_CUDA(cudaMemsetAsync(cnt, 0, 16, st));
+  k_rows_by_kind<<<ceil_div(n_rows, 256), 256, 0, st>>>(n_rows, d_rows, ctx->dense_idx, sparse,
+                                                         dense, cnt);
+  MOCHY_LAUNCHED();
+  unsigned long long hc[2] = {0, 0};
+  MOCHY_CUDA(cudaMemcpyAsync(hc, cnt, 16, cudaMemcpyDeviceToHost, st));
+  MOCHY_CUDA(cudaStreamSynchronize(st));
+  SplitPlan plan;
+  MOCHY_TRY(plan_split(ctx, d_hist, timer.stats, &plan));
+  WorkLists wl;
+  wl.centres = d_rows;
+  wl.n_centres = n_rows;
+  wl.sparse = sparse;
+  wl.n_sparse = (int64_t)hc[0];
+  wl.dense = dense;
+  wl.n_dense = (int64_t)hc[1];
+  MOCHY_TRY(launch_split<false>(ctx, plan, &timer, wl));
   timer.report(ctx);
   return MOCHY_OK;
 }
@@ -1668,8 +1772,8 @@ int count_split_graph(mochy_ctx* ctx, unsigned long long* d_hist, float* ms) {
   if (cudaMemsetAsync(d_hist, 0, (size_t)ctx->n_units * 432 * 8, st) != cudaSuccess)
     rc = fail(MOCHY_E_CUDA, "histogram clear failed during capture");
   if (rc == MOCHY_OK)
-    rc = ctx->n_units > 1 ? launch_split<true>(ctx, plan, nullptr)
-                          : launch_split<false>(ctx, plan, nullptr);
+    rc = ctx->n_units > 1 ? launch_split<true>(ctx, plan, nullptr, all_rows(ctx))
+                          : launch_split<false>(ctx, plan, nullptr, all_rows(ctx));
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(st, &graph);
   if (rc == MOCHY_OK && ec != cudaSuccess)

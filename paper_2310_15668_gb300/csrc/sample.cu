@@ -286,7 +286,10 @@ __global__ void __launch_bounds__(512) k_noalloc_finish(
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Device address of g_noalloc_scratch on the current device, looked up once.
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device and kept for the life of the process.  A device reset
+// (cudaDeviceReset) or a new primary context invalidates the kept address;
+// callers that reset a device must not use this entry point afterwards.
 static int noalloc_scratch(int device, unsigned char** out) {
   static std::mutex mu;
   static unsigned char* addr[256] = {nullptr};

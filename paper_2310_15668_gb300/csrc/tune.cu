@@ -69,6 +69,7 @@ int choose_dense_threshold(mochy_ctx* ctx) {
       nd_all += nd;
     }
     if (dense_smem_bytes(wmax) + 1024 > ctx->smem_optin) continue;
+    if (wmax > kMaxWindowWords) continue;
     if (sparse_smem_bytes((int)std::max<int64_t>(max_sparse, 1)) + 1024 > ctx->smem_optin) continue;
     if (best < 0 || cost < best_cost) {
       best = (int)thr;

@@ -194,3 +194,30 @@ def batch_spec(seed: int, index: int, lo: int, hi: int, alpha: float = 2.5,
     e = loguniform_edges(seed, index, lo, hi)
     return HypergraphSpec(max(e // 2, 64), e, 2, 25, "powerlaw", alpha, "zipf", zipf_s,
                           seed=seed * 1_000_003 + index)
+
+
+def plant_cluster(offsets, nodes, n_extra: int, pool_lo: int, pool_size: int, s_lo: int,
+                  s_hi: int, seed: int):
+    """Append ``n_extra`` hyperedges drawn from a small pool of nodes.
+
+    Each new hyperedge has a size uniform in [s_lo, s_hi] and takes that many
+    distinct nodes of the pool [pool_lo, pool_lo + pool_size) (the nodes with
+    the smallest keys of one SplitMix64 draw per pool node).  Hyperedges drawn
+    from one small pool overlap heavily with each other, which the Zipf and
+    uniform laws above almost never produce.  Returns ``(offsets, nodes)`` of
+    the input followed by the new hyperedges (repeats are left in; loading a
+    hypergraph drops them)."""
+    off = np.asarray(offsets, dtype=np.int64)
+    nod = np.asarray(nodes, dtype=np.int32)
+    ids = np.arange(n_extra, dtype=np.int64)
+    u = _uniform01(seed, 9, ids)
+    sizes = s_lo + np.minimum((u * (s_hi - s_lo + 1)).astype(np.int64), s_hi - s_lo)
+    ctr = ids[:, None] * np.int64(1 << 16) + np.arange(pool_size, dtype=np.int64)[None, :]
+    keys = _uniform01(seed, 10, ctr.ravel()).reshape(n_extra, pool_size)
+    order = np.argsort(keys, axis=1, kind="stable")
+    rows = [np.sort(order[r, :sizes[r]]) + pool_lo for r in range(n_extra)]
+    new_off = np.zeros(n_extra + 1, dtype=np.int64)
+    np.cumsum(sizes, out=new_off[1:])
+    out_off = np.concatenate([off, off[-1] + new_off[1:]])
+    out_nodes = np.concatenate([nod] + [r.astype(np.int32) for r in rows]) if n_extra else nod
+    return out_off, out_nodes

@@ -129,3 +129,72 @@ def test_empty_and_degenerate_graphs():
         off, nodes = _util.csr_from_sets([frozenset(s) for s in sets])
         h, h3 = oracle.count_exact(off, nodes)
         assert h.sum() == 0 and h3.sum() == 0
+
+
+def _owned_brute_force(sets, anchor, rank, theta=1):
+    """Instances the outer-loop iteration of `anchor` counts under a total
+    order `rank` (Algorithm "exact_motif_counting" with i < min(j, k) read as
+    rank[i] < min(rank[j], rank[k])): every connected triple that holds the
+    anchor and either has it as the centre of an open instance (adjacent to
+    both others, which are disjoint) or, when closed, has it lowest-ranked.
+    Enumerated from the node sets, {canonical tuple: count}."""
+    out = {}
+    x = sets[anchor]
+    others = [i for i in range(len(sets)) if i != anchor]
+    for a in range(len(others)):
+        for b in range(a + 1, len(others)):
+            j, k = others[a], others[b]
+            y, z = sets[j], sets[k]
+            if not (x & y and x & z):
+                continue                      # the anchor must be adjacent to both
+            if y & z and not (rank[anchor] < rank[j] and rank[anchor] < rank[k]):
+                continue                      # closed: owned by its lowest-ranked member
+            c = _util.canonical_of_sets(x, y, z, theta)
+            out[c] = out.get(c, 0) + 1
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_ranked_anchor_owns_what_brute_force_says(T, seed):
+    """A fixed total order decides which anchor counts a closed instance;
+    per anchor the oracle's ranked subset equals the instances enumerated
+    from the sets under that order."""
+    sets = _util.micro_graph(700 + seed, n_nodes=11, n_edges=22, s_max=5)
+    off, nodes = _util.csr_from_sets(sets)
+    rank = np.random.default_rng(seed).permutation(len(sets)).astype(np.int64)
+    for anchor in range(len(sets)):
+        h, h3 = oracle.count_exact_ranked(off, nodes, [anchor], rank)
+        assert _util.counts_by_tuple(T["t_pattern"], h3) == _owned_brute_force(sets, anchor, rank)
+
+
+def test_any_order_counts_every_instance_once():
+    """Summed over all anchors, every total order gives the exact count, on
+    several host threads as on one."""
+    spec = synth.HypergraphSpec(400, 900, 2, 12, "powerlaw", 2.5, "zipf", 0.8, seed=9)
+    off, nodes = synth.generate(spec)
+    h, h3 = oracle.count_exact(off, nodes)
+    e = off.size - 1
+    everyone = np.arange(e, dtype=np.int32)
+    for seed in range(3):
+        rank = np.random.default_rng(seed).permutation(e).astype(np.int64)
+        rh, r3 = oracle.count_exact_ranked(off, nodes, everyone, rank, threads=3)
+        assert np.array_equal(rh, h) and np.array_equal(r3, h3)
+    th, t3 = oracle.count_exact_threads(off, nodes, threads=4)
+    assert np.array_equal(th, h) and np.array_equal(t3, h3)
+    # with no order given, ids are compared: the plain subset call
+    part = everyone[::7]
+    assert all(np.array_equal(a, b) for a, b in
+               zip(oracle.count_exact_ranked(off, nodes, part),
+                   oracle.count_exact_subset(off, nodes, part)))
+
+
+def test_line_degrees_from_incidence_lists():
+    """|N_e| from the incidence lists equals the degree in the projected
+    line graph, and Σ_e |N_e| = 2 |wedges|."""
+    for spec in (synth.TINY, synth.HypergraphSpec(300, 700, 2, 25, "powerlaw", 2.5, "zipf",
+                                                  1.0, seed=2)):
+        off, nodes = synth.generate(spec)
+        nw, md, deg = oracle.project(off, nodes)
+        ld = oracle.line_degrees(off, nodes, threads=3)
+        assert np.array_equal(ld, deg)
+        assert int(ld.sum()) == 2 * nw and int(ld.max()) == md

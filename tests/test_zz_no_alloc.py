@@ -1,15 +1,19 @@
-"""The allocation-free sampled count against the regular one (needs a GPU).
+"""The allocation-free sampled count against the regular one and the oracle
+(needs a GPU).
 
 mochy_count_sampled_noalloc serves callers that cannot allocate device memory
 while they run; it keeps its working memory in one fixed array inside the
 library, shared by all calls.  Two calls in a row (different methods, sample
-counts and seeds) must each give what mochy_count_sampled gives on the same
-draws: raw counts equal, estimates within 1e-12 relative.  This file is
-collected last and also runs alone in a fresh process.
+counts and seeds) must each give, bit for bit, what mochy_count_sampled and
+the oracle give on the same Philox draws: raw counts equal as int64 and FP64
+estimates equal (both sides scale the same integers by the same operations
+in the same order).  This file is collected last and also runs alone in a
+fresh process.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_2310_15668_gb300 import binding as B, synth
 
 pytestmark = pytest.mark.gpu
@@ -36,11 +40,13 @@ def test_noalloc_matches_regular_entry_point_twice_in_a_row():
                                           raw_3h.data_ptr(), est_h.data_ptr(), est_3h.data_ptr())
             stream.synchronize()
             assert B.mochy_device_bytes(ctx.h) == before        # nothing allocated
+            got = (raw_h.cpu().numpy(), raw_3h.cpu().numpy(), est_h.cpu().numpy(),
+                   est_3h.cpu().numpy())
             ref = ctx.count_sampled(method, samples, seed)
-            assert np.array_equal(raw_h.cpu().numpy(), ref[0])
-            assert np.array_equal(raw_3h.cpu().numpy(), ref[1])
-            np.testing.assert_allclose(est_h.cpu().numpy(), ref[2], rtol=1e-12, atol=0)
-            np.testing.assert_allclose(est_3h.cpu().numpy(), ref[3], rtol=1e-12, atol=0)
+            orc = oracle.count_sampled(off, nodes, method, samples, seed)
+            for a, b, o in zip(got, ref, orc):
+                assert np.array_equal(a, b)
+                assert np.array_equal(a, o)
             assert ref[0].sum() > 0
 
 
