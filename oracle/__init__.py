@@ -284,3 +284,79 @@ def profile(n_nodes: int, offsets, nodes, n_random: int, seed: int, theta: int =
         _p(c3), _p(deg)), "profile")
     return dict(sig_h=sig_h, cp_h=cp_h, sig_3h=sig_3h, cp_3h=cp_3h, counts_h=ch,
                 counts_3h=c3, degenerate=deg)
+
+
+def kh_tables(k: int):
+    """kh-motif tables for k states: dict of lut[k^7] (code = sum_p state_p
+    k^p -> id, 0 none), pattern [X(k), 7], to_h [X(k)]."""
+    lib = _load()
+    lib.orc_kh_tables.restype = ctypes.c_int64
+    lut = np.zeros(k ** 7, np.int32)
+    n = int(lib.orc_kh_tables(ctypes.c_int(k), _p(lut), None, None, ctypes.c_int64(0)))
+    if n < 0:
+        raise ValueError(f"oracle kh_tables failed for k={k}")
+    pat = np.zeros((n, 7), np.uint8)
+    to_h = np.zeros(n, np.int32)
+    lib.orc_kh_tables(ctypes.c_int(k), _p(lut), _p(pat), _p(to_h), ctypes.c_int64(n))
+    return dict(lut=lut, pattern=pat, to_h=to_h)
+
+
+def count_exact_kh(offsets, nodes, k: int, thresholds):
+    """Exact kh-motif counts (k states, k - 2 ascending thresholds):
+    returns (h counts [26], kh counts [X(k)])."""
+    off, nod = _csr(offsets, nodes)
+    thr = np.ascontiguousarray(thresholds, dtype=np.int32)
+    if thr.size != k - 2:
+        raise ValueError("k - 2 thresholds are needed")
+    n = kh_tables(k)["to_h"].size
+    h = np.zeros(N_H, np.int64)
+    kh = np.zeros(n, np.int64)
+    _check(_load().orc_count_exact_kh(ctypes.c_int64(off.size - 1), _p(off), _p(nod),
+                                      ctypes.c_int32(k),
+                                      _p(thr if thr.size else np.zeros(1, np.int32)),
+                                      _p(h), _p(kh)), "count_exact_kh")
+    return h, kh
+
+
+def radial_node_profile(n_nodes: int, offsets, nodes, theta: int = 1):
+    """Radial node profiles (Section 3.1, "Node Profile (NP)", radial
+    ego-networks): row v counts the instances of each h-motif / 3h-motif
+    among the hyperedges contained in the union of the hyperedges that hold
+    v.  Returns (np_h [N, 26], np_3h [N, 431])."""
+    off, nod = _csr(offsets, nodes)
+    np_h = np.zeros((max(n_nodes, 1), N_H), np.int64)
+    np_3h = np.zeros((max(n_nodes, 1), N_3H), np.int64)
+    _check(_load().orc_radial_node_profile(ctypes.c_int64(n_nodes), ctypes.c_int64(off.size - 1),
+                                           _p(off), _p(nod), ctypes.c_int32(theta), _p(np_h),
+                                           _p(np_3h)), "radial_node_profile")
+    return np_h[:n_nodes], np_3h[:n_nodes]
+
+
+def enumerate_instances(offsets, nodes, theta: int = 1, cap: int | None = None):
+    """Algorithm "alg:enum": every instance as a row (i, j, k, h id, 3h id),
+    ids ascending within the row, in the order the algorithm meets them."""
+    off, nod = _csr(offsets, nodes)
+    n_out = np.zeros(1, np.int64)
+    if cap is None:
+        h, _ = count_exact(off, nod, theta)
+        cap = int(h.sum())
+    out = np.zeros((max(cap, 1), 5), np.int32)
+    _check(_load().orc_enumerate(ctypes.c_int64(off.size - 1), _p(off), _p(nod),
+                                 ctypes.c_int32(theta), ctypes.c_int64(cap), _p(out),
+                                 _p(n_out)), "enumerate")
+    n = int(n_out[0])
+    return out[:min(n, cap)].copy(), n
+
+
+def significance_cp(M, sum_rand, n_random: int, eps: float = 1.0):
+    """Eq. "significance" and Eq. "cp" from the input's counts and the counts
+    summed over n_random copies: (significances, CP, degenerate)."""
+    m = np.ascontiguousarray(M, dtype=np.int64)
+    s = np.ascontiguousarray(sum_rand, dtype=np.int64)
+    sig = np.zeros(m.size)
+    cp = np.zeros(m.size)
+    deg = np.zeros(1, np.int32)
+    _check(_load().orc_significance_cp(_p(m), _p(s), ctypes.c_int32(n_random),
+                                       ctypes.c_int32(m.size), ctypes.c_double(eps), _p(sig),
+                                       _p(cp), _p(deg)), "significance_cp")
+    return sig, cp, bool(deg[0])

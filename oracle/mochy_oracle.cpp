@@ -60,6 +60,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <set>
 #include <unordered_map>
 #include <unordered_set>
@@ -244,6 +245,74 @@ Tables build_tables() {
 const Tables& tables() {
   static const Tables T = build_tables();
   return T;
+}
+
+// kh-motifs (Section 4.1 "Extensions Beyond Ternary"): each region takes one
+// of k states, 0 for empty and s for a cardinality c with
+// thr[s-2] < c <= thr[s-1] (thr[-1] = 0, thr[k-2] = infinity).  Patterns are
+// canonicalised, filtered and numbered as the 3h-motifs are (readings R1,
+// R2: ascending (h-motif id, canonical tuple)).
+struct KTables {
+  int k = 0;
+  std::vector<int32_t> lut;        // k^7 codes (digit p has weight k^p) -> id or 0
+  std::vector<Pattern> pattern;    // index id-1
+  std::vector<int32_t> to_h;       // index id-1 -> h id
+};
+
+KTables build_k_tables(int k) {
+  const Tables& T = tables();
+  KTables K;
+  K.k = k;
+  int64_t total = 1;
+  for (int r = 0; r < 7; ++r) total *= k;
+  auto decode = [&](int64_t code) {
+    Pattern p{};
+    for (int r = 0; r < 7; ++r) { p[r] = (int)(code % k); code /= k; }
+    return p;
+  };
+  std::set<Pattern> valid;
+  for (int64_t code = 0; code < total; ++code) {
+    Pattern c = canonical(decode(code));
+    if (connected(c) && distinct(c)) valid.insert(c);
+  }
+  auto parent = [&](const Pattern& c) {
+    int b = 0;
+    for (int r = 0; r < 7; ++r) b |= (c[r] > 0 ? 1 : 0) << r;
+    return T.lut_h[b];
+  };
+  std::vector<std::pair<std::pair<int, Pattern>, Pattern>> order;
+  for (auto& c : valid) order.push_back({{parent(c), c}, c});
+  std::sort(order.begin(), order.end());
+  std::map<Pattern, int> id;
+  for (size_t n = 0; n < order.size(); ++n) {
+    id[order[n].second] = (int)n + 1;
+    K.pattern.push_back(order[n].second);
+    K.to_h.push_back(order[n].first.first);
+  }
+  K.lut.assign((size_t)total, 0);
+  for (int64_t code = 0; code < total; ++code) {
+    auto it = id.find(canonical(decode(code)));
+    K.lut[(size_t)code] = it == id.end() ? 0 : it->second;
+  }
+  return K;
+}
+
+const KTables& k_tables(int k) {
+  static std::map<int, KTables> cache;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(k);
+  if (it == cache.end()) it = cache.emplace(k, build_k_tables(k)).first;
+  return it->second;
+}
+
+// state of a region of cardinality c among k states with the k - 2
+// ascending thresholds thr: 0 when empty, else 1 + the number exceeded
+int k_state(int64_t c, int k, const int32_t* thr) {
+  if (c == 0) return 0;
+  int s = 1;
+  for (int m = 0; m < k - 2; ++m) s += c > thr[m] ? 1 : 0;
+  return s;
 }
 
 // ---------------------------------------------------------------------------
@@ -934,6 +1003,165 @@ int orc_profile(int64_t n_nodes, int64_t n_edges, const int64_t* off,
   significance_cp(counts_3h, mr_3h.data(), 431, eps, sig_3h, cp_3h, &d2);
   degenerate[0] = d1;
   degenerate[1] = d2;
+  return 0;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Extensions: kh-motifs, radial node profiles, instance enumeration, the
+// significance and CP on their own.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+// kh-motif tables for k states (Section 4.1 "Extensions Beyond Ternary";
+// their number is X(k) of Appendix "Number of kH-motifs"): lut has k^7
+// entries (code = sum_p state_p k^p -> id, 0 = no motif); pattern (n x 7)
+// and to_h (n) are filled for the n motifs when non-null and n <= cap.
+int64_t orc_kh_tables(int k, int32_t* lut, uint8_t* pattern, int32_t* to_h, int64_t cap) {
+  if (k < 2 || k > 6) return -1;
+  const KTables& K = k_tables(k);
+  const int64_t n = (int64_t)K.pattern.size();
+  if (lut) std::memcpy(lut, K.lut.data(), K.lut.size() * sizeof(int32_t));
+  if (n <= cap) {
+    for (int64_t i = 0; i < n; ++i) {
+      if (pattern)
+        for (int r = 0; r < 7; ++r) pattern[i * 7 + r] = (uint8_t)K.pattern[i][r];
+      if (to_h) to_h[i] = K.to_h[i];
+    }
+  }
+  return n;
+}
+
+// Exact kh-motif counts: Algorithm "exact_motif_counting" with h(.) replaced
+// by the k-state classification of the seven regions (Section 4.1; the
+// regions from Lemma "motif:time").  thr holds the k - 2 ascending
+// thresholds; out_kh has X(k) entries, out_h 26.
+int orc_count_exact_kh(int64_t n_edges, const int64_t* off, const int32_t* nodes, int32_t k,
+                       const int32_t* thr, int64_t* out_h, int64_t* out_kh) {
+  if (k < 2 || k > 6) return -1;
+  for (int m = 0; m + 1 < k - 2; ++m)
+    if (thr[m] < 1 || thr[m + 1] <= thr[m]) return -1;
+  if (k > 2 && thr[0] < 1) return -1;
+  Hypergraph G;
+  if (build(n_edges, off, nodes, G)) return -1;
+  LineGraph L = project(G);
+  const KTables& K = k_tables(k);
+  std::fill(out_h, out_h + 26, 0);
+  std::fill(out_kh, out_kh + K.pattern.size(), 0);
+  const int64_t E = (int64_t)G.e.size();
+  for (int64_t i = 0; i < E; ++i) {
+    const auto& N = L.nbr[i];
+    for (size_t x = 0; x < N.size(); ++x)
+      for (size_t y = x + 1; y < N.size(); ++y) {
+        const int32_t j = N[x], kk = N[y];
+        const int32_t wjk = omega_of(L, j, kk);
+        if (!(wjk == 0 || i < std::min(j, kk))) continue;
+        auto r = regions(G, i, j, kk, omega_of(L, i, j), wjk, omega_of(L, kk, i));
+        int64_t code = 0, pw = 1;
+        for (int p = 0; p < 7; ++p) {
+          code += k_state(r[p], k, thr) * pw;
+          pw *= k;
+        }
+        const int id = K.lut[(size_t)code];
+        if (id <= 0) return -2;
+        out_kh[id - 1] += 1;
+        out_h[K.to_h[id - 1] - 1] += 1;
+      }
+  }
+  return 0;
+}
+
+// Radial node profiles (Section 3.1, "Node Profile (NP)" with the radial
+// ego-network of "Hypergraph Ego-networks"): V_v is the union of the
+// hyperedges that contain v, R_v the hyperedges that are subsets of V_v; the
+// radial ego-network of v is (V_v, R_v) and its instances are the connected
+// triples of R_v, counted here by MoCHy-E on that subhypergraph.  Hyperedges
+// are kept whole, so regions and motifs are those in G.  np_h is n_nodes x
+// 26, np_3h n_nodes x 431; either may be null.
+int orc_radial_node_profile(int64_t n_nodes, int64_t n_edges, const int64_t* off,
+                            const int32_t* nodes, int32_t theta, int64_t* np_h,
+                            int64_t* np_3h) {
+  Hypergraph G;
+  if (build(n_edges, off, nodes, G)) return -1;
+  if (np_h) std::fill(np_h, np_h + n_nodes * 26, 0);
+  if (np_3h) std::fill(np_3h, np_3h + n_nodes * 431, 0);
+  for (const auto& kv : G.ev) {
+    const int64_t v = kv.first;
+    if (v < 0 || v >= n_nodes) return -1;
+    std::unordered_set<int32_t> Vv;
+    for (int32_t e : kv.second) Vv.insert(G.e[e].begin(), G.e[e].end());
+    Hypergraph R;   // (V_v, R_v), hyperedges in the order of G
+    for (size_t i = 0; i < G.e.size(); ++i) {
+      bool inside = true;
+      for (int32_t u : G.e[i]) inside = inside && Vv.count(u) > 0;
+      if (inside) R.e.push_back(G.e[i]);
+    }
+    for (size_t i = 0; i < R.e.size(); ++i) {
+      R.eset.emplace_back(R.e[i].begin(), R.e[i].end());
+      for (int32_t u : R.e[i]) R.ev[u].push_back((int32_t)i);
+    }
+    LineGraph L = project(R);
+    int64_t h[26], h3[431];
+    exact_count(R, L, theta, nullptr, h, h3);
+    for (int t = 0; t < 26; ++t)
+      if (np_h) np_h[v * 26 + t] = h[t];
+    for (int t = 0; t < 431; ++t)
+      if (np_3h) np_3h[v * 431 + t] = h3[t];
+  }
+  return 0;
+}
+
+// Algorithm "alg:enum" (MoCHy-E_ENUM): every instance written once with its
+// motifs, as (i, j, k, h, 3h) with the three ids ascending (ids after
+// duplicate removal); *n_out receives the number of instances, of which the
+// first min(n, cap) are written to out (cap x 5) in the order the algorithm
+// meets them.
+int orc_enumerate(int64_t n_edges, const int64_t* off, const int32_t* nodes, int32_t theta,
+                  int64_t cap, int32_t* out, int64_t* n_out) {
+  Hypergraph G;
+  if (build(n_edges, off, nodes, G)) return -1;
+  LineGraph L = project(G);
+  const int64_t E = (int64_t)G.e.size();
+  int64_t n = 0;
+  for (int64_t i = 0; i < E; ++i) {
+    const auto& N = L.nbr[i];
+    for (size_t x = 0; x < N.size(); ++x)
+      for (size_t y = x + 1; y < N.size(); ++y) {
+        const int32_t j = N[x], k = N[y];
+        const int32_t wjk = omega_of(L, j, k);
+        if (!(wjk == 0 || i < std::min(j, k))) continue;
+        auto r = regions(G, i, j, k, omega_of(L, i, j), wjk, omega_of(L, k, i));
+        int h, h3;
+        classify(r, theta, &h, &h3);
+        if (n < cap) {
+          int32_t ids[3] = {(int32_t)i, j, k};
+          std::sort(ids, ids + 3);
+          int32_t* o = out + n * 5;
+          o[0] = ids[0];
+          o[1] = ids[1];
+          o[2] = ids[2];
+          o[3] = h;
+          o[4] = h3;
+        }
+        ++n;
+      }
+  }
+  *n_out = n;
+  return 0;
+}
+
+// Eq. "significance" and Eq. "cp" for n motifs: M are the input's counts,
+// sum_rand the counts summed over n_random randomized copies (M_rand is
+// their mean, reading R9).
+int orc_significance_cp(const int64_t* M, const int64_t* sum_rand, int32_t n_random, int32_t n,
+                        double eps, double* sig, double* cp, int32_t* degenerate) {
+  if (n_random <= 0 || n <= 0) return -1;
+  std::vector<double> mr(n);
+  for (int t = 0; t < n; ++t) mr[t] = (double)sum_rand[t] / (double)n_random;
+  int d = 0;
+  significance_cp(M, mr.data(), n, eps, sig, cp, &d);
+  *degenerate = d;
   return 0;
 }
 
