@@ -171,6 +171,51 @@ int mochy_hyperedge_profile(mochy_ctx* ctx, int64_t* hp_h, int64_t* hp_3h);
  * Radial and contracted node profiles are not provided. */
 int mochy_star_node_profile(mochy_ctx* ctx, int64_t* np_h, int64_t* np_3h);
 
+/* Radial node profiles (Section 3.1, "Node Profile (NP)" with the radial
+ * ego-network of v: node set V_v = the union of the hyperedges that contain
+ * v, hyperedges R_v = the hyperedges that are subsets of V_v):
+ * np_h[v * 26 + t - 1] / np_3h[v * 431 + t - 1] count the instances of
+ * h-motif / 3h-motif t among the hyperedges of R_v (host arrays of n_nodes
+ * rows; either may be NULL).  Hyperedges are kept whole, so every instance
+ * is classified as in G.  One CTA per node marks V_v and R_v in bitmaps and
+ * counts the instances among R_v (Algorithm "exact_motif_counting" with the
+ * neighbours outside R_v skipped); the work is the sum over nodes of
+ * sum_{e in R_v} |N_e|^2, so the call suits small hypergraphs.  Needs
+ * mochy_project, 3.5 KB of device memory per node and (n_nodes / 8 +
+ * n_edges * 4.2) bytes per resident CTA while it runs.  Rows of star
+ * profiles (mochy_star_node_profile) never exceed these. */
+int mochy_radial_node_profile(mochy_ctx* ctx, int64_t* np_h, int64_t* np_3h);
+
+/* kh-motif counts (Section 4.1, "Extensions Beyond Ternary"): each of the
+ * seven regions takes one of k states (2 <= k <= 4): 0 when empty, else 1
+ * plus the number of the k - 2 ascending thresholds (host int32, values in
+ * [1, 63]) its cardinality exceeds; k = 3 with threshold theta gives the
+ * 3h-motifs, k = 4 has X(4) = 3,076 motifs (Appendix "Number of kH-motifs").
+ * Patterns are canonicalised and filtered as for 3h-motifs and numbered in
+ * ascending (parent h-motif id, canonical tuple) order (mochy_kh_pattern).
+ * out_kh[t-1] (cap >= X(k) entries, may be NULL) receives the count of
+ * kh-motif t, out_h (26, may be NULL) the h-motif counts, *n_motifs (may be
+ * NULL) X(k).  Instances are enumerated one by one by the per-hyperwedge
+ * scan (exact_kernel = 1's kernel, at most about 300,000 hyperedges).
+ * Needs mochy_project. */
+int mochy_count_kh(mochy_ctx* ctx, int32_t k, const int32_t* thresholds, int64_t* out_h,
+                   int64_t* out_kh, int64_t cap, int64_t* n_motifs);
+
+/* Region states (regions (1)..(7) of Section 2.2) of kh-motif `id` for k
+ * states; MOCHY_E_INVALID for an id outside 1..X(k). */
+int mochy_kh_pattern(mochy_ctx* ctx, int32_t k, int32_t id, uint8_t regions_out[7]);
+
+/* Instance enumeration (MoCHy-E_ENUM, Algorithm "alg:enum", Section 3.2):
+ * every instance of every motif, written once as a row of five int32
+ * (i, j, k, h-motif id, 3h-motif id) with i < j < k hyperedge ids, into
+ * h_out (host, capacity rows), in no particular order.  *n_instances
+ * receives the number of instances (the sum of mochy_count_exact's counts);
+ * when it exceeds capacity only `capacity` of them are written.  The rows
+ * are produced on the device by the per-hyperwedge scan into a stream of
+ * capacity * 20 bytes (budget-checked) and copied out.  Needs
+ * mochy_project. */
+int mochy_enumerate(mochy_ctx* ctx, int64_t capacity, int32_t* h_out, int64_t* n_instances);
+
 /* Sampled counts.  method MOCHY_A draws `samples` hyperedges uniformly with
  * replacement (Algorithm "sampling_ver1"); MOCHY_A_PLUS draws `samples`
  * hyperwedges (Algorithm "sampling_ver2").  Draw n uses Philox4x32-10 with

@@ -30,7 +30,8 @@ EXPORTS = [
     "mochy_motif_pattern", "mochy_stream", "mochy_device_bytes", "mochy_kernel_launches",
     "mochy_strerror", "mochy_last_error", "mochy_trace", "mochy_trace_read",
     "mochy_count_sampled_noalloc", "mochy_profile_batch", "mochy_server_create",
-    "mochy_hyperedge_profile", "mochy_star_node_profile",
+    "mochy_hyperedge_profile", "mochy_star_node_profile", "mochy_radial_node_profile",
+    "mochy_count_kh", "mochy_kh_pattern", "mochy_enumerate",
     "mochy_server_submit", "mochy_server_poll", "mochy_server_stats", "mochy_server_destroy",
 ]
 MOCHY_REQ_EXACT, MOCHY_REQ_SAMPLED, MOCHY_REQ_PROFILE = 1, 2, 3
@@ -149,6 +150,10 @@ def load_library(path: str = LIB_PATH):
                                                 ctypes.POINTER(mochy_batch_info)]
             lib.mochy_hyperedge_profile.argtypes = [vp, vp, vp]
             lib.mochy_star_node_profile.argtypes = [vp, vp, vp]
+            lib.mochy_radial_node_profile.argtypes = [vp, vp, vp]
+            lib.mochy_count_kh.argtypes = [vp, i32, vp, vp, vp, i64, vp]
+            lib.mochy_kh_pattern.argtypes = [vp, i32, i32, vp]
+            lib.mochy_enumerate.argtypes = [vp, i64, vp, vp]
             lib.mochy_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(mochy_config),
                                                 i32, i32]
             lib.mochy_server_submit.argtypes = [vp, ctypes.POINTER(mochy_request),
@@ -315,6 +320,44 @@ def mochy_star_node_profile(ctx: int, n_nodes: int):
     return np_h[:n_nodes], np_3h[:n_nodes]
 
 
+def mochy_radial_node_profile(ctx: int, n_nodes: int):
+    """Radial node profiles of the projected hypergraph: (np_h [N, 26], np_3h [N, 431])."""
+    np_h = np.zeros((max(n_nodes, 1), N_H), np.int64)
+    np_3h = np.zeros((max(n_nodes, 1), N_3H), np.int64)
+    _check(load_library().mochy_radial_node_profile(ctx, _p(np_h), _p(np_3h)),
+           "mochy_radial_node_profile")
+    return np_h[:n_nodes], np_3h[:n_nodes]
+
+
+def mochy_count_kh(ctx: int, k: int, thresholds=()):
+    """kh-motif counts: (h counts [26], kh counts [X(k)])."""
+    thr = np.ascontiguousarray(thresholds, dtype=np.int32)
+    n = np.zeros(1, np.int64)
+    lib = load_library()
+    _check(lib.mochy_count_kh(ctx, k, _p(thr if thr.size else np.zeros(1, np.int32)), None, None,
+                              0, _p(n)), "mochy_count_kh")
+    h = np.zeros(N_H, np.int64)
+    kh = np.zeros(max(int(n[0]), 1), np.int64)
+    _check(lib.mochy_count_kh(ctx, k, _p(thr if thr.size else np.zeros(1, np.int32)), _p(h),
+                              _p(kh), kh.size, _p(n)), "mochy_count_kh")
+    return h, kh[:int(n[0])]
+
+
+def mochy_kh_pattern(ctx: int, k: int, motif_id: int) -> np.ndarray:
+    out = np.zeros(7, np.uint8)
+    _check(load_library().mochy_kh_pattern(ctx, k, motif_id, _p(out)), "mochy_kh_pattern")
+    return out
+
+
+def mochy_enumerate(ctx: int, capacity: int):
+    """Instances as rows (i, j, k, h id, 3h id), i < j < k, in no particular
+    order: (rows [min(n, capacity), 5], n)."""
+    out = np.zeros((max(capacity, 1), 5), np.int32)
+    n = np.zeros(1, np.int64)
+    _check(load_library().mochy_enumerate(ctx, capacity, _p(out), _p(n)), "mochy_enumerate")
+    return out[:min(int(n[0]), capacity)], int(n[0])
+
+
 def mochy_profile_batch(graphs, n_random: int, seeds, cfg: mochy_config | None = None):
     """Profiles of several hypergraphs at once.  graphs: list of
     (n_nodes, offsets, nodes); seeds: one per graph.  Returns
@@ -437,6 +480,16 @@ class Context:
     def star_node_profile(self):
         n_nodes, _, _ = self.hypergraph()
         return mochy_star_node_profile(self.h, n_nodes)
+
+    def radial_node_profile(self):
+        n_nodes, _, _ = self.hypergraph()
+        return mochy_radial_node_profile(self.h, n_nodes)
+
+    def count_kh(self, k, thresholds=()):
+        return mochy_count_kh(self.h, k, thresholds)
+
+    def enumerate(self, capacity):
+        return mochy_enumerate(self.h, capacity)
 
     def hypergraph(self):
         return mochy_get_hypergraph(self.h)

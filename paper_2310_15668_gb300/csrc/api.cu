@@ -270,6 +270,7 @@ int mochy_destroy(mochy_ctx* ctx) {
   if (ctx->hist) cudaFree(ctx->hist);
   if (ctx->stats) cudaFree(ctx->stats);
   if (ctx->tables.lut3) cudaFree(ctx->tables.lut3);
+  if (ctx->kh_block) cudaFree(ctx->kh_block);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -503,6 +504,122 @@ int mochy_star_node_profile(mochy_ctx* ctx, int64_t* np_h, int64_t* np_3h) {
       for (int t = 1; t <= MOCHY_N_3H; ++t) o[t2h[t] - 1] += (int64_t)r[t];
     }
   }
+  return MOCHY_OK;
+}
+
+int mochy_radial_node_profile(mochy_ctx* ctx, int64_t* np_h, int64_t* np_3h) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  MOCHY_TRY(device_guard(ctx));
+  if (!ctx->projected) return fail(MOCHY_E_NOT_PROJECTED, "call mochy_project first");
+  const int64_t N = ctx->n_nodes;
+  if (N == 0) return MOCHY_OK;
+  const size_t bytes = (size_t)N * 432 * 8;
+  void* d = nullptr;
+  MOCHY_TRY(dev_alloc(ctx, &d, bytes));
+  std::vector<unsigned long long> h((size_t)N * 432);
+  uint8_t t2h[432];
+  int rc = radial_node_profiles(ctx, (unsigned long long*)d);
+  if (rc == MOCHY_OK &&
+      (cudaMemcpyAsync(h.data(), d, bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+       cudaMemcpyAsync(t2h, ctx->tables.t2h, 432, cudaMemcpyDeviceToHost, ctx->stream) !=
+           cudaSuccess ||
+       cudaStreamSynchronize(ctx->stream) != cudaSuccess))
+    rc = fail(MOCHY_E_CUDA, "profile copy failed");
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(ctx, d, bytes);
+  if (rc < 0) return rc;
+  for (int64_t v = 0; v < N; ++v) {
+    const unsigned long long* r = h.data() + (size_t)v * 432;
+    if (r[0] != 0ull) return fail(MOCHY_E_CUDA, "internal error: an instance mapped to no motif");
+    if (np_3h)
+      for (int t = 1; t <= MOCHY_N_3H; ++t) np_3h[v * MOCHY_N_3H + t - 1] = (int64_t)r[t];
+    if (np_h) {
+      int64_t* o = np_h + v * MOCHY_N_H;
+      for (int t = 0; t < MOCHY_N_H; ++t) o[t] = 0;
+      for (int t = 1; t <= MOCHY_N_3H; ++t) o[t2h[t] - 1] += (int64_t)r[t];
+    }
+  }
+  return MOCHY_OK;
+}
+
+int mochy_count_kh(mochy_ctx* ctx, int32_t k, const int32_t* thresholds, int64_t* out_h,
+                   int64_t* out_kh, int64_t cap, int64_t* n_motifs) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  if (k < 2 || k > 4) return fail(MOCHY_E_UNSUPPORTED, "kh-motifs are provided for k = 2..4");
+  if (k > 2 && !thresholds) return fail(MOCHY_E_INVALID, "thresholds needed");
+  const int thr1 = k > 2 ? thresholds[0] : 1, thr2 = k > 3 ? thresholds[1] : thr1 + 1;
+  if (k > 2 && (thr1 < 1 || thr1 > MOCHY_MAX_EDGE_SIZE))
+    return fail(MOCHY_E_INVALID, "thresholds must lie in [1, 63]");
+  if (k > 3 && (thr2 <= thr1 || thr2 > MOCHY_MAX_EDGE_SIZE))
+    return fail(MOCHY_E_INVALID, "thresholds must ascend");
+  MOCHY_TRY(device_guard(ctx));
+  if (!ctx->projected) return fail(MOCHY_E_NOT_PROJECTED, "call mochy_project first");
+  MOCHY_TRY(build_kh_tables(ctx, k));
+  const int n = ctx->kh_n;
+  if (n_motifs) *n_motifs = n;
+  if (out_kh && cap < n) return fail(MOCHY_E_INVALID, "out_kh holds fewer than X(k) entries");
+  const size_t bytes = (size_t)(n + 1) * 8;
+  void* d = nullptr;
+  MOCHY_TRY(dev_alloc(ctx, &d, bytes));
+  std::vector<unsigned long long> h((size_t)n + 1);
+  std::vector<uint8_t> to_h((size_t)n + 1);
+  int rc = count_kh(ctx, k, thr1, thr2, (unsigned long long*)d);
+  if (rc == MOCHY_OK &&
+      (cudaMemcpyAsync(h.data(), d, bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+       cudaMemcpyAsync(to_h.data(), ctx->kh_to_h, (size_t)n + 1, cudaMemcpyDeviceToHost,
+                       ctx->stream) != cudaSuccess ||
+       cudaStreamSynchronize(ctx->stream) != cudaSuccess))
+    rc = fail(MOCHY_E_CUDA, "kh count copy failed");
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(ctx, d, bytes);
+  if (rc < 0) return rc;
+  if (h[0] != 0ull) return fail(MOCHY_E_CUDA, "internal error: an instance mapped to no motif");
+  if (out_kh)
+    for (int t = 1; t <= n; ++t) out_kh[t - 1] = (int64_t)h[t];
+  if (out_h) {
+    for (int t = 0; t < MOCHY_N_H; ++t) out_h[t] = 0;
+    for (int t = 1; t <= n; ++t) out_h[to_h[t] - 1] += (int64_t)h[t];
+  }
+  return MOCHY_OK;
+}
+
+int mochy_kh_pattern(mochy_ctx* ctx, int32_t k, int32_t id, uint8_t* regions_out) {
+  if (!ctx || !regions_out) return fail(MOCHY_E_INVALID, "null argument");
+  MOCHY_TRY(device_guard(ctx));
+  MOCHY_TRY(build_kh_tables(ctx, k));
+  if (id < 1 || id > ctx->kh_n) return fail(MOCHY_E_INVALID, "no such kh-motif");
+  MOCHY_CUDA(cudaMemcpyAsync(regions_out, ctx->kh_pattern + (size_t)id * 7, 7,
+                             cudaMemcpyDeviceToHost, ctx->stream));
+  MOCHY_CUDA(cudaStreamSynchronize(ctx->stream));
+  return MOCHY_OK;
+}
+
+int mochy_enumerate(mochy_ctx* ctx, int64_t capacity, int32_t* h_out, int64_t* n_instances) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  if (capacity < 0 || (capacity > 0 && !h_out)) return fail(MOCHY_E_INVALID, "bad output");
+  MOCHY_TRY(device_guard(ctx));
+  if (!ctx->projected) return fail(MOCHY_E_NOT_PROJECTED, "call mochy_project first");
+  const size_t bytes = (size_t)std::max<int64_t>(capacity, 1) * 5 * 4 + 256;
+  void* d = nullptr;
+  MOCHY_TRY(dev_alloc(ctx, &d, bytes));
+  unsigned long long* cursor = (unsigned long long*)d;
+  int32_t* rows = (int32_t*)((char*)d + 256);
+  unsigned long long total = 0;
+  int rc = enumerate_instances(ctx, capacity, rows, cursor);
+  if (rc == MOCHY_OK &&
+      (cudaMemcpyAsync(&total, cursor, 8, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+       cudaStreamSynchronize(ctx->stream) != cudaSuccess))
+    rc = fail(MOCHY_E_CUDA, "enumeration failed");
+  const int64_t written = std::min<int64_t>((int64_t)total, capacity);
+  if (rc == MOCHY_OK && written > 0 &&
+      (cudaMemcpyAsync(h_out, rows, (size_t)written * 5 * 4, cudaMemcpyDeviceToHost,
+                       ctx->stream) != cudaSuccess ||
+       cudaStreamSynchronize(ctx->stream) != cudaSuccess))
+    rc = fail(MOCHY_E_CUDA, "enumeration copy failed");
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(ctx, d, bytes);
+  if (rc < 0) return rc;
+  if (n_instances) *n_instances = (int64_t)total;
   return MOCHY_OK;
 }
 

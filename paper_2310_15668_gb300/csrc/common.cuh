@@ -151,6 +151,15 @@ struct mochy_ctx {
   int64_t* d_dbase = nullptr;          // [n_units+1] first dense index per unit
   int64_t wmax = 0;                    // widest unit window, words
 
+  // kh-motif tables (built on first use): lut over k^7 codes, parent h id
+  // and pattern (7 states) of each id
+  int kh_k = 0, kh_n = 0;
+  void* kh_block = nullptr;
+  size_t kh_bytes = 0;
+  uint16_t* kh_lut = nullptr;
+  uint8_t* kh_to_h = nullptr;
+  uint8_t* kh_pattern = nullptr;
+
   // per-call device scratch
   unsigned long long* hist = nullptr;  // [432] 3h histogram (index = id)
   int32_t* counters = nullptr;         // [16] work-queue counters / flags
@@ -189,6 +198,7 @@ int radix_sort_pairs_u32(mochy_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t
 
 // Stages.
 int build_tables(mochy_ctx* ctx);                                     // tables.cu
+int build_kh_tables(mochy_ctx* ctx, int k);                           // tables.cu
 int load_graph(mochy_ctx* ctx, int64_t n_nodes, int64_t n_edges,
                const int64_t* d_off, const int32_t* d_nodes, int64_t* n_dup);  // load.cu
 int project_graph(mochy_ctx* ctx);                                    // project.cu
@@ -199,6 +209,10 @@ int count_split_rows(mochy_ctx* ctx, const int32_t* d_rows, int64_t n_rows,
                      unsigned long long* d_hist);                     // count_split.cu
 int hyperedge_profiles(mochy_ctx* ctx, unsigned long long* d_hp);    // count_exact.cu
 int star_node_profiles(mochy_ctx* ctx, unsigned long long* d_np);    // count_exact.cu
+int radial_node_profiles(mochy_ctx* ctx, unsigned long long* d_np);  // extensions.cu
+int count_kh(mochy_ctx* ctx, int k, int thr1, int thr2, unsigned long long* d_hist);  // extensions.cu
+int enumerate_instances(mochy_ctx* ctx, int64_t cap, int32_t* d_out,
+                        unsigned long long* d_cursor);                // extensions.cu
 int prepare_split(mochy_ctx* ctx);                                    // count_split.cu
 void release_split(mochy_ctx* ctx);                                   // count_split.cu
 int count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t seed,

@@ -168,7 +168,130 @@ __global__ void __launch_bounds__(512) k_build_tables(uint16_t* lut3, uint8_t* t
   }
 }
 
+// kh-motif tables (Section 4.1 "Extensions Beyond Ternary"), k states per
+// region, k^7 <= 16384 codes; numbered like the 3h-motifs: ascending
+// (parent h-motif id, canonical tuple).  Three passes over the codes.
+// Pass 1: canonical key, validity, representative flag and parent h id (the
+// h id of a binary pattern is read through the 3h tables: its 0/1 digits
+// are a ternary code whose 3h-motif refines exactly that h-motif).
+__global__ void k_kh_keys(int base, int n_codes, const uint16_t* __restrict__ lut3,
+                          const uint8_t* __restrict__ t2h, int* __restrict__ key,
+                          int* __restrict__ hid, unsigned char* __restrict__ rep) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_codes) return;
+  int st[7];
+  for (int r = 0; r < 7; ++r) st[r] = digit(c, base, r);
+  key[c] = canonical_key(c, base);
+  int g;
+  const bool ok = classify_pattern(c, base, &g) != 0;
+  int tc = 0, pw = 1;
+  for (int r = 0; r < 7; ++r) {
+    tc += (st[r] > 0 ? 1 : 0) * pw;
+    pw *= 3;
+  }
+  hid[c] = ok ? (int)t2h[lut3[tc]] : 0;
+  rep[c] = (unsigned char)(ok && lex_key(st, base) == key[c]);
+}
+
+// Pass 2: each representative's id is one plus the number of
+// representatives before it in (h id, key) order.
+__global__ void k_kh_rank(int base, int n_codes, const int* __restrict__ key,
+                          const int* __restrict__ hid, const unsigned char* __restrict__ rep,
+                          int* __restrict__ id_of_key, uint8_t* __restrict__ to_h,
+                          uint8_t* __restrict__ pattern) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_codes || !rep[c]) return;
+  int id = 1;
+  for (int d = 0; d < n_codes; ++d)
+    if (rep[d] && (hid[d] < hid[c] || (hid[d] == hid[c] && key[d] < key[c]))) ++id;
+  id_of_key[key[c]] = id;
+  to_h[id] = (uint8_t)hid[c];
+  for (int r = 0; r < 7; ++r) pattern[id * 7 + r] = (uint8_t)digit(c, base, r);
+}
+
+// Pass 3: the id of every code is its representative's.
+__global__ void k_kh_lut(int n_codes, const int* __restrict__ key, const int* __restrict__ hid,
+                         const int* __restrict__ id_of_key, uint16_t* __restrict__ lut) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_codes) return;
+  lut[c] = hid[c] ? (uint16_t)id_of_key[key[c]] : (uint16_t)0;
+}
+
 }  // namespace
+
+// The kh-motif tables for k states (2 <= k <= 4) into ctx (built once per k
+// and kept with the context).
+int build_kh_tables(mochy_ctx* ctx, int k) {
+  if (k < 2 || k > 4) return fail(MOCHY_E_UNSUPPORTED, "kh-motifs are provided for k = 2..4");
+  if (ctx->kh_k == k) return MOCHY_OK;
+  if (ctx->kh_block) {
+    dev_free(ctx, ctx->kh_block, ctx->kh_bytes);
+    ctx->kh_block = nullptr;
+    ctx->kh_k = 0;
+  }
+  int n_codes = 1;
+  for (int r = 0; r < 7; ++r) n_codes *= k;
+  cudaStream_t st = ctx->stream;
+  const size_t b_lut = ((size_t)n_codes * 2 + 255) & ~(size_t)255;
+  const size_t b_toh = 4096, b_pat = 4096 * 7;
+  const size_t bytes = b_lut + b_toh + b_pat;
+  void* p = nullptr;
+  MOCHY_TRY(dev_alloc(ctx, &p, bytes));
+  void* t = nullptr;
+  const size_t b_tmp = (size_t)n_codes * (4 + 4 + 4 + 1) + 64;
+  const int rc0 = dev_alloc(ctx, &t, b_tmp);
+  if (rc0 < 0) {
+    dev_free(ctx, p, bytes);
+    return rc0;
+  }
+  int* key = (int*)t;
+  int* hid = key + n_codes;
+  int* id_of_key = hid + n_codes;
+  unsigned char* rep = (unsigned char*)(id_of_key + n_codes);
+  uint16_t* lut = (uint16_t*)p;
+  uint8_t* to_h = (uint8_t*)p + b_lut;
+  uint8_t* pat = to_h + b_toh;
+  int rc = MOCHY_OK;
+  if (cudaMemsetAsync(p, 0, bytes, st) != cudaSuccess ||
+      cudaMemsetAsync(id_of_key, 0, (size_t)n_codes * 4, st) != cudaSuccess)
+    rc = fail(MOCHY_E_CUDA, "kh table clear failed");
+  const int nb = (n_codes + 255) / 256;
+  if (rc == MOCHY_OK) {
+    k_kh_keys<<<nb, 256, 0, st>>>(k, n_codes, ctx->tables.lut3, ctx->tables.t2h, key, hid, rep);
+    note_launch();
+    k_kh_rank<<<nb, 256, 0, st>>>(k, n_codes, key, hid, rep, id_of_key, to_h, pat);
+    note_launch();
+    k_kh_lut<<<nb, 256, 0, st>>>(n_codes, key, hid, id_of_key, lut);
+    note_launch();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) rc = cuda_fail(e, "kh table kernels", __FILE__, __LINE__);
+  }
+  int n_motifs = 0;
+  if (rc == MOCHY_OK) {
+    // the number of motifs is the largest id, found on the host
+    std::vector<uint16_t> h((size_t)n_codes);
+    if (cudaMemcpyAsync(h.data(), lut, (size_t)n_codes * 2, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = fail(MOCHY_E_CUDA, "kh table copy failed");
+    } else {
+      for (uint16_t v : h) n_motifs = std::max(n_motifs, (int)v);
+    }
+  }
+  dev_free(ctx, t, b_tmp);
+  if (rc != MOCHY_OK) {
+    dev_free(ctx, p, bytes);
+    return rc;
+  }
+  ctx->kh_block = p;
+  ctx->kh_bytes = bytes;
+  ctx->kh_lut = lut;
+  ctx->kh_to_h = to_h;
+  ctx->kh_pattern = pat;
+  ctx->kh_k = k;
+  ctx->kh_n = n_motifs;
+  return MOCHY_OK;
+}
 
 // Process-wide host copy of the patterns (for mochy_motif_pattern).
 static uint8_t g_pat2[27 * 7], g_pat3[432 * 7];
