@@ -360,3 +360,22 @@ def significance_cp(M, sum_rand, n_random: int, eps: float = 1.0):
                                        ctypes.c_int32(m.size), ctypes.c_double(eps), _p(sig),
                                        _p(cp), _p(deg)), "significance_cp")
     return sig, cp, bool(deg[0])
+
+
+def count_aplus_onthefly(offsets, nodes, method: int, samples: int, seed: int, budget: int,
+                         theta: int = 1):
+    """MoCHy-A+ without the line graph: method 1 = basic (Algorithm
+    "alg_memdeg"), 2 = advanced (Algorithm "alg_memdeg_adv"), memo budget in
+    neighbour entries.  Returns (raw_h, raw_3h, est_h, est_3h, stats) with
+    stats = (getNeighbors calls, evictions, |wedges|)."""
+    off, nod = _csr(offsets, nodes)
+    rh = np.zeros(N_H, np.int64)
+    r3 = np.zeros(N_3H, np.int64)
+    eh = np.zeros(N_H, np.float64)
+    e3 = np.zeros(N_3H, np.float64)
+    st = np.zeros(3, np.int64)
+    _check(_load().orc_count_aplus_onthefly(
+        ctypes.c_int64(off.size - 1), _p(off), _p(nod), ctypes.c_int32(theta), ctypes.c_int(method),
+        ctypes.c_int64(samples), ctypes.c_uint64(seed), ctypes.c_int64(budget), _p(rh), _p(r3),
+        _p(eh), _p(e3), _p(st)), "count_aplus_onthefly")
+    return rh, r3, eh, e3, st

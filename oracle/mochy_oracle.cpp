@@ -1166,3 +1166,207 @@ int orc_significance_cp(const int64_t* M, const int64_t* sum_rand, int32_t n_ran
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// MoCHy-A+ without the line graph (Section 3.4 "Motif Counting without Line
+// Graphs"; Appendix "Details of On-the-Fly MoCHy", Algorithms "alg_memdeg"
+// (basic) and "alg_memdeg_adv" (advanced)).
+//
+// Readings: (R13) a uniformly random hyperwedge is drawn exactly as by
+// MoCHy-A+ (readings R6, R7: index floor(u |wedges| / 2^64) in ascending
+// (i, j) order), so that the on-the-fly runs classify the same hyperwedges
+// as the projected one; the number of neighbours after each hyperedge, which
+// that order needs, comes from the same pass as the degrees d_i.  (R14) the
+// budget b counts memoized neighbour entries (sum of d_l over memoized
+// hyperedges).  (R15) when even an empty memo cannot hold N_{e_l}
+// (d_l > b), N_{e_l} is computed for the current hyperwedge only and not
+// memoized (the eviction loop of the algorithms would not end).
+// ---------------------------------------------------------------------------
+namespace {
+
+// getNeighbors(e, G): hyperedge -> omega over the incidence lists
+std::map<int32_t, int32_t> get_neighbors(const Hypergraph& G, int32_t e) {
+  std::map<int32_t, int32_t> n;
+  for (int32_t v : G.e[e])
+    for (int32_t f : G.ev.at(v))
+      if (f != e) n[f] += 1;
+  return n;
+}
+
+struct OnTheFlyStats {
+  int64_t built = 0;     // getNeighbors calls
+  int64_t evicted = 0;   // neighbourhoods evicted to make room
+};
+
+// The memo A with capacity cap and the priority queue Q of memoized
+// hyperedges, lowest degree popped first (Appendix "on-the-fly": Q
+// prioritizes high-degree hyperedges, so a low-degree one is evicted).
+struct Memo {
+  const Hypergraph& G;
+  const std::vector<int64_t>& d;
+  int64_t cap;
+  std::map<int32_t, std::map<int32_t, int32_t>> A;
+  std::set<std::pair<int64_t, int32_t>> Q;
+  OnTheFlyStats st;
+  Memo(const Hypergraph& g, const std::vector<int64_t>& deg, int64_t b) : G(g), d(deg), cap(b) {}
+
+  bool in_q(int32_t l) const { return Q.count({d[l], l}) > 0; }
+
+  // the body of the "for each l in {i, j}" memo loop for one l; returns
+  // N_{e_l} (memoized, or computed for this use only, reading R15)
+  const std::map<int32_t, int32_t>& fetch(int32_t l, int32_t i, int32_t j,
+                                          std::map<int32_t, int32_t>& scratch) {
+    auto it = A.find(l);
+    if (it != A.end()) return it->second;
+    std::vector<std::pair<int64_t, int32_t>> held;   // popped i or j, pushed back below
+    while (cap < d[l] && !Q.empty()) {
+      auto m = *Q.begin();
+      Q.erase(Q.begin());
+      if (m.second != i && m.second != j) {
+        cap += d[m.second];
+        A.erase(m.second);
+        ++st.evicted;
+      } else {
+        held.push_back(m);
+      }
+    }
+    for (auto& h : held) Q.insert(h);
+    ++st.built;
+    if (cap < d[l]) {
+      scratch = get_neighbors(G, l);
+      return scratch;
+    }
+    A[l] = get_neighbors(G, l);
+    cap -= d[l];
+    Q.insert({d[l], l});
+    return A[l];
+  }
+
+  void drop(int32_t l) {   // Algorithm alg_memdeg_adv: a key's group is done
+    auto it = A.find(l);
+    if (it == A.end()) return;
+    Q.erase({d[l], l});
+    cap += d[l];
+    A.erase(it);
+  }
+};
+
+// The classification of every e_k in N_i u N_j \ {e_i, e_j} (the counting
+// loop shared by both algorithms and by Algorithm "sampling_ver2").
+void count_union(const Hypergraph& G, int32_t theta, int32_t i, int32_t j,
+                 const std::map<int32_t, int32_t>& Ni, const std::map<int32_t, int32_t>& Nj,
+                 int64_t* raw_h, int64_t* raw_3h) {
+  const int64_t wij = Ni.count(j) ? Ni.at(j) : 0;
+  std::set<int32_t> cand;
+  for (auto& kv : Ni) cand.insert(kv.first);
+  for (auto& kv : Nj) cand.insert(kv.first);
+  cand.erase(i);
+  cand.erase(j);
+  for (int32_t k : cand) {
+    auto a = Ni.find(k);
+    auto b = Nj.find(k);
+    const int64_t wik = a == Ni.end() ? 0 : a->second;
+    const int64_t wjk = b == Nj.end() ? 0 : b->second;
+    auto r = regions(G, i, j, k, wij, wjk, wik);
+    int h, h3;
+    classify(r, theta, &h, &h3);
+    raw_h[h - 1] += 1;
+    raw_3h[h3 - 1] += 1;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+// method 1 = basic (Algorithm "alg_memdeg"), 2 = advanced
+// (Algorithm "alg_memdeg_adv"); budget = b in neighbour entries.  Estimates
+// as Algorithm "sampling_ver2" (open w = 2, closed w = 3).  stats (may be
+// null): getNeighbors calls, evictions.
+int orc_count_aplus_onthefly(int64_t n_edges, const int64_t* off, const int32_t* nodes,
+                             int32_t theta, int method, int64_t samples, uint64_t seed,
+                             int64_t budget, int64_t* raw_h, int64_t* raw_3h, double* est_h,
+                             double* est_3h, int64_t* stats) {
+  Hypergraph G;
+  if (build(n_edges, off, nodes, G)) return -1;
+  if (samples <= 0 || budget < 0 || (method != 1 && method != 2)) return -1;
+  const int64_t E = (int64_t)G.e.size();
+  // the degrees d_i in the line graph, and the neighbours after each i
+  std::vector<int64_t> d(E, 0), up(E, 0);
+  for (int64_t i = 0; i < E; ++i) {
+    auto n = get_neighbors(G, (int32_t)i);
+    d[i] = (int64_t)n.size();
+    for (auto& kv : n) up[i] += kv.first > i ? 1 : 0;
+  }
+  std::vector<int64_t> upre(E + 1, 0);
+  for (int64_t i = 0; i < E; ++i) upre[i + 1] = upre[i] + up[i];
+  const uint64_t nw = (uint64_t)upre[E];
+  if (nw == 0) return -1;
+  // the n-th sampled hyperwedge (reading R13)
+  auto sample = [&](int64_t n, Memo& memo, std::map<int32_t, int32_t>& scratch) {
+    const int64_t w = (int64_t)scale_index(draw_u64(seed, (uint64_t)n, kStreamWedgeSample, 0), nw);
+    const int64_t i = (int64_t)(std::upper_bound(upre.begin(), upre.end(), w) - upre.begin()) - 1;
+    const auto& Ni = memo.fetch((int32_t)i, (int32_t)i, -1, scratch);
+    int64_t o = w - upre[i];
+    int32_t j = -1;
+    for (auto& kv : Ni)
+      if (kv.first > i && o-- == 0) { j = kv.first; break; }
+    return std::make_pair((int32_t)i, j);
+  };
+  std::fill(raw_h, raw_h + 26, 0);
+  std::fill(raw_3h, raw_3h + 431, 0);
+  Memo memo(G, d, budget);
+  std::map<int32_t, int32_t> si, sj;
+  if (method == 1) {
+    for (int64_t n = 0; n < samples; ++n) {
+      auto ij = sample(n, memo, si);
+      const int32_t i = ij.first, j = ij.second;
+      // for each l in {i, j}: memoized or fetched (Algorithm alg_memdeg)
+      std::map<int32_t, int32_t> Ni = memo.fetch(i, i, j, si);
+      const auto& Nj = memo.fetch(j, i, j, sj);
+      for (int32_t l : {i, j})
+        if (memo.A.count(l) && !memo.in_q(l)) memo.Q.insert({d[l], l});
+      count_union(G, theta, i, j, Ni, Nj, raw_h, raw_3h);
+    }
+  } else {
+    // collect the r hyperwedges, grouped by their key hyperedge (the one of
+    // larger (d, id)), then processed in descending (d, id) of the keys
+    std::map<std::pair<int64_t, int32_t>, std::vector<std::pair<int32_t, int32_t>>,
+             std::greater<std::pair<int64_t, int32_t>>> W;
+    // (a draw reads N_{e_i} through the same memo, reading R13)
+    for (int64_t n = 0; n < samples; ++n) {
+      auto ij = sample(n, memo, si);
+      const int32_t i = ij.first, j = ij.second;
+      const bool i_key = d[i] > d[j] || (d[i] == d[j] && i > j);
+      const int32_t key = i_key ? i : j;
+      W[{d[key], key}].push_back(ij);
+    }
+    for (auto& grp : W) {
+      const int32_t key = grp.first.second;
+      for (auto& ij : grp.second) {
+        const int32_t i = ij.first, j = ij.second;
+        std::map<int32_t, int32_t> Ni = memo.fetch(i, i, j, si);
+        const auto& Nj = memo.fetch(j, i, j, sj);
+        count_union(G, theta, i, j, Ni, Nj, raw_h, raw_3h);
+      }
+      memo.drop(key);
+    }
+  }
+  const Tables& T = tables();
+  for (int t = 0; t < 26; ++t) {
+    const double w = T.h_open[t] ? 2.0 : 3.0;
+    est_h[t] = (double)raw_h[t] * (double)nw / (w * (double)samples);
+  }
+  for (int t = 0; t < 431; ++t) {
+    const double w = T.h_open[T.t_to_h[t] - 1] ? 2.0 : 3.0;
+    est_3h[t] = (double)raw_3h[t] * (double)nw / (w * (double)samples);
+  }
+  if (stats) {
+    stats[0] = memo.st.built;
+    stats[1] = memo.st.evicted;
+    stats[2] = (int64_t)nw;
+  }
+  return 0;
+}
+
+}  // extern "C"
