@@ -17,7 +17,10 @@ device-to-host read of the counts.  roofline: the dominant kernel's duration
 is taken live from the library's traced CUDA events.  cpu_baseline: the
 CPU oracle (its anchor loop on every host core) on a seeded anchor sample of
 the same hypergraph.  sampled: candidates classified/s of MoCHy-A+ with
-r = 2,000,000 hyperwedges on the same projected hypergraph.
+r = 2,000,000 hyperwedges on the same projected hypergraph.  onthefly (rank
+0, one GPU): MoCHy-A+ without the line graph on the large workload (1.5M
+nodes, 2.5M hyperedges, Zipf(1.1), seed 2; its line graph would need 6 to
+12 TB), r = 2,000,000.
 
 batch (rank 0, one GPU): significance and CP of 16 seeded hypergraphs (E
 log-uniform in [2,000, 20,000], N = E/2, power-law sizes on [2, 25], Zipf(1.0)
@@ -256,6 +259,56 @@ def _sampled_measure(ctx, args):
             "calls": args.sampled_steps}
 
 
+def _onthefly_measure(args):
+    """MoCHy-A+ without the line graph on the large workload (1.5M nodes,
+    2.5M hyperedges, sizes s^-2.2 on [2, 25], Zipf(1.1) members, seed 2):
+    r = 2,000,000 hyperwedges drawn by Philox seed 2.  Its line graph (4e11
+    to 8e11 hyperwedges) does not fit in device memory.  The first call
+    after the load builds the membership bitmaps and the line-graph degrees
+    (reported as set-up); the timed calls classify r draws each.  Device
+    time with CUDA events on the library's stream."""
+    import torch
+    from paper_2310_15668_gb300 import binding as B, synth
+    t = time.perf_counter()
+    off, nodes = synth.generate(synth.LARGE)
+    gen_s = time.perf_counter() - t
+    r = int(args.onthefly_r)
+    with B.Context() as c:
+        stream = torch.cuda.ExternalStream(c.stream)
+        c.load(synth.LARGE.n_nodes, off, nodes)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        first = c.count_sampled_onthefly(1, 2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        setup_ms = e0.elapsed_time(e1)
+        times, cands = [], 0
+        for k in range(args.sampled_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            raw_h, _, est_h, _, nw = c.count_sampled_onthefly(r, 2 + k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            cands = int(raw_h.sum())
+        B.mochy_trace(c.h, 2)
+        c.count_sampled_onthefly(r, 2)
+        tr = B.mochy_trace_read(c.h)
+    ms = float(np.mean(times))
+    return {"metric": "candidates classified/s (MoCHy-A+ without the line graph)",
+            "value": cands / (ms / 1000.0), "unit": "candidates/s", "r": r,
+            "candidates_per_call": cands, "ms_per_call": ms, "calls": args.sampled_steps,
+            "setup_ms": setup_ms, "hyperwedges": int(first[4]),
+            "config": {"workload": f"large: {synth.LARGE.describe()}, r = {r} hyperwedges by "
+                                   f"Philox seed 2 (+ call index)",
+                       "line_graph_bytes_if_projected": int(first[4]) * 16},
+            "generate_s": gen_s,
+            "trace": {k: tr.get(k) for k in ("otf_candidates", "otf_words", "otf_list_entries",
+                                             "otf_exact", "otf_bitmaps")}}
+
+
 def _batch_measure(args):
     """CPs/s of the batched profile against one profile call per hypergraph."""
     from paper_2310_15668_gb300 import binding as B, synth
@@ -459,9 +512,11 @@ def run_gpu(args):
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = _cpu_baseline(off, nodes, spec.n_nodes, args.cpu_seconds)
-    batch = serving = None
+    batch = serving = onthefly = None
     if ws == 1 and not args.no_extras:
         ctx.close()                       # free the medium line graph first
+        if args.onthefly_r > 0:
+            onthefly = _onthefly_measure(args)
         batch = _batch_measure(args)
         serving = _serving_measure(args)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -472,7 +527,7 @@ def run_gpu(args):
                        "parallelism": f"independent hypergraph per rank x{ws}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk.summary(), "phases_ms": avg, "trace": st, "sampled": sampled,
-            "batch": batch, "serving": serving}
+            "onthefly": onthefly, "batch": batch, "serving": serving}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -492,6 +547,8 @@ def main():
     ap.add_argument("--sampled-r", type=int, default=2_000_000,
                     help="MoCHy-A+ samples of the candidates/s line (0: skip)")
     ap.add_argument("--sampled-steps", type=int, default=3)
+    ap.add_argument("--onthefly-r", type=int, default=2_000_000,
+                    help="MoCHy-A+ draws on the large workload without a line graph (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-seconds", type=float, default=10.0)

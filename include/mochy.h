@@ -229,6 +229,27 @@ int mochy_count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t se
                         int64_t raw_h[MOCHY_N_H], int64_t raw_3h[MOCHY_N_3H],
                         double est_h[MOCHY_N_H], double est_3h[MOCHY_N_3H]);
 
+/* MoCHy-A+ without the line graph (Section 3.4, "Motif Counting without
+ * Line Graphs"; Algorithms "alg_memdeg" and "alg_memdeg_adv"): the same
+ * estimator as mochy_count_sampled(MOCHY_A_PLUS) with the same draws
+ * (draw n is hyperwedge floor(u |wedges| / 2^64) of the ascending (i, j)
+ * order, Philox4x32-10 counter (n_lo, n_hi, 2, 0), key seed), so raw counts
+ * and estimates are identical to the projected call's, but it needs only
+ * mochy_load: no line graph is built.  Neighbourhoods are never stored;
+ * the hyperedge-id space is scanned per drawn hyperwedge with membership
+ * bitmaps of the most popular nodes (as many as budget_bytes allows; <= 0:
+ * a quarter of the context's budget, else 4 GiB) and the incidence lists of
+ * the others.  The bitmaps, the line-graph degrees and their prefix are
+ * built by the first call after a load and kept until the next load (the
+ * budget of later calls is then ignored; results never depend on it).
+ * *n_wedges (may be NULL) receives |wedges|.  Output pointers may be NULL.
+ * With mochy_trace level 2, mochy_trace_read reports candidates, scanned
+ * words, list entries and node-list classifications of the call. */
+int mochy_count_sampled_onthefly(mochy_ctx* ctx, int64_t samples, uint64_t seed,
+                                 int64_t budget_bytes, int64_t raw_h[MOCHY_N_H],
+                                 int64_t raw_3h[MOCHY_N_3H], double est_h[MOCHY_N_H],
+                                 double est_3h[MOCHY_N_3H], int64_t* n_wedges);
+
 /* Sampled counts as mochy_count_sampled, written to caller-provided DEVICE
  * arrays (d_raw_h[26], d_raw_3h[431] int64; d_est_h[26], d_est_3h[431] FP64),
  * without allocating any device memory.  The paper has no counterpart: this

@@ -31,7 +31,7 @@ EXPORTS = [
     "mochy_strerror", "mochy_last_error", "mochy_trace", "mochy_trace_read",
     "mochy_count_sampled_noalloc", "mochy_profile_batch", "mochy_server_create",
     "mochy_hyperedge_profile", "mochy_star_node_profile", "mochy_radial_node_profile",
-    "mochy_count_kh", "mochy_kh_pattern", "mochy_enumerate",
+    "mochy_count_kh", "mochy_kh_pattern", "mochy_enumerate", "mochy_count_sampled_onthefly",
     "mochy_server_submit", "mochy_server_poll", "mochy_server_stats", "mochy_server_destroy",
 ]
 MOCHY_REQ_EXACT, MOCHY_REQ_SAMPLED, MOCHY_REQ_PROFILE = 1, 2, 3
@@ -154,6 +154,8 @@ def load_library(path: str = LIB_PATH):
             lib.mochy_count_kh.argtypes = [vp, i32, vp, vp, vp, i64, vp]
             lib.mochy_kh_pattern.argtypes = [vp, i32, i32, vp]
             lib.mochy_enumerate.argtypes = [vp, i64, vp, vp]
+            lib.mochy_count_sampled_onthefly.argtypes = [vp, i64, ctypes.c_uint64, i64, vp, vp,
+                                                         vp, vp, vp]
             lib.mochy_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(mochy_config),
                                                 i32, i32]
             lib.mochy_server_submit.argtypes = [vp, ctypes.POINTER(mochy_request),
@@ -343,6 +345,19 @@ def mochy_count_kh(ctx: int, k: int, thresholds=()):
     return h, kh[:int(n[0])]
 
 
+def mochy_count_sampled_onthefly(ctx: int, samples: int, seed: int, budget: int = 0):
+    """MoCHy-A+ without the line graph: (raw_h, raw_3h, est_h, est_3h, |wedges|)."""
+    rh = np.zeros(N_H, np.int64)
+    r3 = np.zeros(N_3H, np.int64)
+    eh = np.zeros(N_H, np.float64)
+    e3 = np.zeros(N_3H, np.float64)
+    nw = np.zeros(1, np.int64)
+    _check(load_library().mochy_count_sampled_onthefly(ctx, samples, seed, budget, _p(rh),
+                                                        _p(r3), _p(eh), _p(e3), _p(nw)),
+           "mochy_count_sampled_onthefly")
+    return rh, r3, eh, e3, int(nw[0])
+
+
 def mochy_kh_pattern(ctx: int, k: int, motif_id: int) -> np.ndarray:
     out = np.zeros(7, np.uint8)
     _check(load_library().mochy_kh_pattern(ctx, k, motif_id, _p(out)), "mochy_kh_pattern")
@@ -490,6 +505,9 @@ class Context:
 
     def enumerate(self, capacity):
         return mochy_enumerate(self.h, capacity)
+
+    def count_sampled_onthefly(self, samples, seed, budget=0):
+        return mochy_count_sampled_onthefly(self.h, samples, seed, budget)
 
     def hypergraph(self):
         return mochy_get_hypergraph(self.h)

@@ -138,6 +138,7 @@ void release_projection(mochy_ctx* ctx) {
 
 void release_graph(mochy_ctx* ctx) {
   release_projection(ctx);
+  release_onthefly(ctx);
   if (ctx->eoff) {
     cudaStreamSynchronize(ctx->stream);
     dev_free(ctx, ctx->eoff, graph_bytes(ctx, 0));
@@ -623,6 +624,47 @@ int mochy_enumerate(mochy_ctx* ctx, int64_t capacity, int32_t* h_out, int64_t* n
   return MOCHY_OK;
 }
 
+int mochy_count_sampled_onthefly(mochy_ctx* ctx, int64_t samples, uint64_t seed,
+                                 int64_t budget_bytes, int64_t* raw_h, int64_t* raw_3h,
+                                 double* est_h, double* est_3h, int64_t* n_wedges) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  if (!ctx->eoff) return fail(MOCHY_E_INVALID, "no hypergraph loaded");
+  if (ctx->n_units != 1) return fail(MOCHY_E_INVALID, "a lone hypergraph is needed");
+  MOCHY_TRY(device_guard(ctx));
+  unsigned long long* d_stats = nullptr;
+  if (ctx->trace > 1) {
+    if (!ctx->stats) {
+      void* p;
+      MOCHY_TRY(dev_alloc(ctx, &p, 88 * sizeof(unsigned long long)));
+      ctx->stats = (unsigned long long*)p;
+    }
+    d_stats = ctx->stats;
+  }
+  MOCHY_TRY(count_sampled_onthefly(ctx, samples, seed, budget_bytes, ctx->hist, d_stats));
+  int64_t* d_counts = (int64_t*)((char*)ctx->counters + 64);
+  double* d_est = (double*)(d_counts + 457);
+  MOCHY_CUDA(cudaMemsetAsync(ctx->counters + 8, 0, 4, ctx->stream));
+  MOCHY_TRY(finish_counts(ctx, ctx->hist, d_counts, d_counts + MOCHY_N_H));
+  MOCHY_TRY(scale_estimates(ctx, d_counts, d_counts + MOCHY_N_H, MOCHY_A_PLUS,
+                            (double)ctx->otf_wedges, samples, d_est, d_est + MOCHY_N_H));
+  int64_t* h = (int64_t*)ctx->pinned;
+  MOCHY_CUDA(cudaMemcpyAsync(h, d_counts, 457 * 16, cudaMemcpyDeviceToHost, ctx->stream));
+  if (d_stats)
+    MOCHY_CUDA(cudaMemcpyAsync(ctx->last_stats + 19, d_stats, 4 * 8, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  MOCHY_CUDA(cudaStreamSynchronize(ctx->stream));
+  int32_t bad = 0;
+  MOCHY_CUDA(cudaMemcpy(&bad, ctx->counters + 8, 4, cudaMemcpyDeviceToHost));
+  if (bad) return fail(MOCHY_E_CUDA, "internal error: an instance mapped to no motif");
+  const double* he = (const double*)(h + 457);
+  if (raw_h) memcpy(raw_h, h, MOCHY_N_H * 8);
+  if (raw_3h) memcpy(raw_3h, h + MOCHY_N_H, MOCHY_N_3H * 8);
+  if (est_h) memcpy(est_h, he, MOCHY_N_H * 8);
+  if (est_3h) memcpy(est_3h, he + MOCHY_N_H, MOCHY_N_3H * 8);
+  if (n_wedges) *n_wedges = ctx->otf_wedges;
+  return MOCHY_OK;
+}
+
 int mochy_count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t seed,
                         int64_t* raw_h, int64_t* raw_3h, double* est_h, double* est_3h) {
   if (!ctx) return fail(MOCHY_E_INVALID, "null context");
@@ -756,7 +798,7 @@ int mochy_trace_read(mochy_ctx* ctx, char* buf, int64_t len) {
              ctx->phase_ms[i]);
     js += item;
   }
-  char tail[1024];
+  char tail[2048];
   const unsigned long long* st = ctx->last_stats;
   snprintf(tail, sizeof(tail),
            "}, \"dense_rows\": %lld, \"dense_threshold\": %d, \"dense_words\": %lld, "
@@ -766,10 +808,12 @@ int mochy_trace_read(mochy_ctx* ctx, char* buf, int64_t len) {
            "\"clk_groups\": %llu, \"clk_light\": %llu, \"clk_sort\": %llu, "
            "\"light_entries\": %llu, \"dense_hyperwedges\": %llu, \"light_nodes\": %llu, "
            "\"heavy_bitmaps\": %llu, \"slots_evicted\": %llu, \"slots_flushed_full\": %llu, "
-           "\"dense_rows_counted\": %llu}",
+           "\"dense_rows_counted\": %llu, \"otf_candidates\": %llu, \"otf_words\": %llu, "
+           "\"otf_list_entries\": %llu, \"otf_exact\": %llu, \"otf_bitmaps\": %lld}",
            (long long)ctx->n_dense, ctx->dense_thr_used, (long long)ctx->wwords,
            (long long)ctx->n_heavy, st[0], st[1], st[2], st[3], st[4], st[5], st[6], st[7], st[8],
-           st[9], st[10], st[11], st[12], st[13], st[14], st[16], st[17], st[18]);
+           st[9], st[10], st[11], st[12], st[13], st[14], st[16], st[17], st[18], st[19],
+           st[20], st[21], st[22], (long long)ctx->otf_bitmaps);
   js += tail;
   if ((int64_t)js.size() + 1 > len) return fail(MOCHY_E_INVALID, "buffer too small");
   memcpy(buf, js.c_str(), js.size() + 1);

@@ -151,6 +151,18 @@ struct mochy_ctx {
   int64_t* d_dbase = nullptr;          // [n_units+1] first dense index per unit
   int64_t wmax = 0;                    // widest unit window, words
 
+  // MoCHy-A+ without the line graph (built on first use after a load):
+  // membership bitmaps of the most popular nodes, size planes, and the
+  // prefix of the number of neighbours after each hyperedge
+  bool otf_ready = false;
+  void* otf_block = nullptr;
+  size_t otf_bytes = 0;
+  int32_t* otf_hidx = nullptr;     // [N] bitmap index or -1
+  uint32_t* otf_hbits = nullptr;   // [otf_bitmaps][otf_words]
+  uint32_t* otf_sbits = nullptr;   // [4][otf_words]
+  int64_t* otf_uprefix = nullptr;  // [E+1]
+  int64_t otf_wedges = 0, otf_bitmaps = 0, otf_words = 0;
+
   // kh-motif tables (built on first use): lut over k^7 codes, parent h id
   // and pattern (7 states) of each id
   int kh_k = 0, kh_n = 0;
@@ -211,6 +223,9 @@ int hyperedge_profiles(mochy_ctx* ctx, unsigned long long* d_hp);    // count_ex
 int star_node_profiles(mochy_ctx* ctx, unsigned long long* d_np);    // count_exact.cu
 int radial_node_profiles(mochy_ctx* ctx, unsigned long long* d_np);  // extensions.cu
 int count_kh(mochy_ctx* ctx, int k, int thr1, int thr2, unsigned long long* d_hist);  // extensions.cu
+int count_sampled_onthefly(mochy_ctx* ctx, int64_t samples, uint64_t seed, int64_t budget,
+                           unsigned long long* d_hist, unsigned long long* d_stats);  // onthefly.cu
+void release_onthefly(mochy_ctx* ctx);                                // onthefly.cu
 int enumerate_instances(mochy_ctx* ctx, int64_t cap, int32_t* d_out,
                         unsigned long long* d_cursor);                // extensions.cu
 int prepare_split(mochy_ctx* ctx);                                    // count_split.cu
