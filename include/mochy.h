@@ -344,7 +344,11 @@ int mochy_profile_batch(const mochy_config* cfg, int32_t n_graphs, const int64_t
  * request runs exactly the calls a direct caller would make (mochy_load,
  * mochy_project, then mochy_count_exact, mochy_count_sampled or
  * mochy_profile) on a context of its own: its result is the same alone and
- * in any mix.  The functions may be called from any host thread. */
+ * in any mix.  A MoCHy-A+ request whose line graph would take more than a
+ * quarter of the budget runs without one (mochy_count_sampled_onthefly,
+ * identical results, n_wedges reported the same way), so hypergraphs whose
+ * line graph does not fit the device can still be served.  The functions
+ * may be called from any host thread. */
 typedef struct mochy_server mochy_server;
 
 #define MOCHY_REQ_EXACT 1    /* exact counts (Algorithm "exact_motif_counting") */

@@ -8,7 +8,9 @@
 // streams.  Every request runs the same library calls as a direct caller
 // would (mochy_load, mochy_project, then mochy_count_exact,
 // mochy_count_sampled or mochy_profile) on a context of its own, so its
-// result does not depend on what else is running.
+// result does not depend on what else is running.  A MoCHy-A+ request
+// whose line graph would take more than a quarter of the budget is run
+// without it (mochy_count_sampled_onthefly: same draws, same counts).
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -41,6 +43,8 @@ struct Request {
   int32_t n_random = 0;
   uint64_t seed = 0;
   int64_t est = 0;
+  bool onthefly = false;     // MoCHy-A+ without the line graph
+  int64_t otf_budget = 0;    // its bitmap budget, bytes
   double t_submit = 0.0;
 };
 
@@ -87,6 +91,16 @@ namespace {
 void run_request(mochy_ctx* ctx, const Request& r, mochy_result& out) {
   int rc = mochy_load(ctx, r.n_nodes, (int64_t)r.off.size() - 1, r.off.data(),
                       r.nodes.empty() ? nullptr : r.nodes.data(), nullptr);
+  if (rc >= 0 && r.onthefly) {
+    // same draws and counts as the projected call, without the line graph
+    rc = mochy_count_sampled_onthefly(ctx, r.samples, r.seed, r.otf_budget, out.counts_h,
+                                      out.counts_3h, out.est_h, out.est_3h, &out.n_wedges);
+    out.status = rc;
+    if (rc < 0) snprintf(out.error, sizeof(out.error), "%s", mochy_last_error());
+    release_graph(ctx);
+    release_scratch(ctx);
+    return;
+  }
   if (rc >= 0) rc = mochy_project(ctx, &out.n_wedges, nullptr);
   if (rc >= 0) {
     switch (r.kind) {
@@ -244,6 +258,15 @@ int mochy_server_submit(mochy_server* s, const mochy_request* req, int64_t* tick
   // a profile holds the input and one copy at a time
   r->est = estimate_graph_bytes(req->n_nodes, req->n_edges, req->edge_offsets, req->edge_nodes) *
            (req->kind == MOCHY_REQ_PROFILE ? 2 : 1);
+  // a MoCHy-A+ request whose line graph would take more than a quarter of
+  // the budget runs without it (identical results; the memory is the
+  // hypergraph, the degree arrays and the membership bitmaps)
+  if (req->kind == MOCHY_REQ_SAMPLED && req->method == MOCHY_A_PLUS && r->est > s->budget / 4) {
+    r->onthefly = true;
+    r->otf_budget = std::min<int64_t>(s->budget / 8, (int64_t)1 << 30);
+    r->est = (int64_t)(64.0 * (double)req->n_edges + 48.0 * (double)T +
+                       20.0 * (double)req->n_nodes) + r->otf_budget + ((int64_t)1 << 20);
+  }
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->setup_rc < 0) return fail(s->setup_rc, "a server slot failed to start");
   if (r->est > s->budget) {

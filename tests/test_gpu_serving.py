@@ -131,3 +131,20 @@ def test_queue_full_and_bad_requests():
         with pytest.raises(B.MochyError) as e:
             srv.submit(B.MOCHY_REQ_SAMPLED, *g, samples=0)
         assert e.value.code == B.E_INVALID
+
+
+def test_large_aplus_requests_run_without_the_line_graph():
+    """A MoCHy-A+ request whose line graph would take more than a quarter of
+    the budget is served without it: admitted with the smaller reservation,
+    and its raw counts, estimates and |wedges| equal the projected call's."""
+    g = _zipf(5000, 80)
+    est = _estimate(*g)
+    with B.Server(n_slots=2, budget=2 * est) as srv:
+        t = srv.submit(B.MOCHY_REQ_SAMPLED, *g, samples=4000, seed=9)
+        r = srv.poll(t, wait_ms=120000)
+        st = srv.stats()
+    _check_same(r, _alone(B.MOCHY_REQ_SAMPLED, g, samples=4000, seed=9))
+    assert 0 < st["peak_reserved_bytes"] < est
+    with B.Context() as c:
+        c.load(*g)
+        assert r["n_wedges"] == c.project()[0]
