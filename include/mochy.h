@@ -134,18 +134,24 @@ int mochy_count_exact_subset(mochy_ctx* ctx, const int32_t* h_anchors,
                              int64_t n_anchors, int64_t out_h[MOCHY_N_H],
                              int64_t out_3h[MOCHY_N_3H]);
 
-/* The part of the exact count that the split kernel (exact_kernel = 0)
- * adds for the rows h_rows[0..n_rows) (host int32 hyperedge ids; an id may
- * not repeat): open instances centred at a listed row, plus closed
- * instances whose first member in the split kernel's row order is listed.
- * That order puts the rows of line degree below the dense threshold T
- * first, ascending by id, then the rows of line degree >= T ascending by
- * (line degree, id); T is cfg.dense_threshold when set, else the tuner's
- * choice (mochy_trace_read reports it).  This is Algorithm
- * "exact_motif_counting" (Section 3.2) with its id comparison i < min(j, k)
- * replaced by that order; any fixed total order counts every instance once,
- * so summed over all rows it equals mochy_count_exact.  Needs mochy_project;
- * MOCHY_E_INVALID for the scan kernel or a batch. */
+/* The share of the rows h_rows[0..n_rows) (host int32 hyperedge ids; an id
+ * may not repeat) in the split kernel's exact count (exact_kernel = 0).  The
+ * split kernel counts open instances per centre from all pairs of its
+ * neighbours: for a centre e_c and neighbours e_p, e_q whose overlaps with
+ * e_c fit in it, the pair is classified "as if open" (the regions of Lemma
+ * "motif:time" with omega(p, q) = 0 and no triple intersection); a closed
+ * instance is then added at its first member in the kernel's row order,
+ * with its as-if-open terms at its three centres taken off.  A row's share
+ * is its pairs as if open plus those corrections of the closed instances it
+ * owns, so shares can be negative; summed over all rows they give the exact
+ * count of Algorithm "exact_motif_counting" (Section 3.2), since any fixed
+ * order owns every closed instance once.  The row order puts rows of line
+ * degree below the dense threshold T first, ascending by id, then the rows
+ * of line degree >= T ascending by (line degree, id); T is
+ * cfg.dense_threshold when set, else the tuner's choice (mochy_trace_read
+ * reports it).  Meant for checking the kernel at full size on a sample of
+ * rows.  Needs mochy_project; MOCHY_E_INVALID for the scan kernel or a
+ * batch. */
 int mochy_count_exact_rows(mochy_ctx* ctx, const int32_t* h_rows, int64_t n_rows,
                            int64_t out_h[MOCHY_N_H], int64_t out_3h[MOCHY_N_3H]);
 

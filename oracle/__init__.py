@@ -379,3 +379,23 @@ def count_aplus_onthefly(offsets, nodes, method: int, samples: int, seed: int, b
         ctypes.c_int64(samples), ctypes.c_uint64(seed), ctypes.c_int64(budget), _p(rh), _p(r3),
         _p(eh), _p(e3), _p(st)), "count_aplus_onthefly")
     return rh, r3, eh, e3, st
+
+
+def count_split_rows(offsets, nodes, rows, rank=None, theta: int = 1, threads: int = 1):
+    """Per-row shares of the exact count when open instances are counted per
+    centre from all neighbour pairs: for each row r, every pair of its
+    neighbours classified as if open at r, plus, for each closed instance
+    whose lowest-ranked member is r, its motif minus its three as-if-open
+    terms.  Summed over all rows this is the exact count.  (h [26], 3h [431]),
+    entries may be negative."""
+    off, nod = _csr(offsets, nodes)
+    rw = np.ascontiguousarray(rows, dtype=np.int32)
+    rk = None if rank is None else np.ascontiguousarray(rank, dtype=np.int64)
+    h = np.zeros(N_H, np.int64)
+    h3 = np.zeros(N_3H, np.int64)
+    nt = host_threads() if threads == 0 else int(threads)
+    _check(_load().orc_count_split_rows(
+        ctypes.c_int64(off.size - 1), _p(off), _p(nod), ctypes.c_int32(theta),
+        _p(rw if rw.size else np.zeros(1, np.int32)), ctypes.c_int64(rw.size),
+        None if rk is None else _p(rk), ctypes.c_int32(nt), _p(h), _p(h3)), "count_split_rows")
+    return h, h3

@@ -1370,3 +1370,95 @@ int orc_count_aplus_onthefly(int64_t n_edges, const int64_t* off, const int32_t*
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Per-row shares of the exact count when open instances are counted per
+// centre from all pairs of its neighbours (the decomposition the library's
+// split count uses; not one of the paper's algorithms, but an identity
+// between its counts).
+//
+// For a centre e_c and neighbours e_p, e_q with omega(c,p) + omega(c,q) <=
+// |e_c|, "as if open" classifies {c; p, q} with the regions of an open
+// instance centred at c (Lemma "motif:time" with omega(p,q) = 0 and no
+// triple intersection).  An open instance is met exactly so at its centre
+// and nowhere else; a closed instance is met so at each of its three
+// centres where the condition holds.  Hence the exact count (Algorithm
+// "exact_motif_counting") equals the sum over rows r of
+//   (every pair of neighbours of r, as if open at r)
+// + (for each closed instance whose first member in `rank` is r: its motif,
+//    minus its "as if open" term at each of its three centres),
+// which is what the share of a row is.  Shares may be negative.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int orc_count_split_rows(int64_t n_edges, const int64_t* off, const int32_t* nodes,
+                         int32_t theta, const int32_t* rows, int64_t n_rows, const int64_t* rank,
+                         int32_t threads, int64_t* out_h, int64_t* out_3h) {
+  Hypergraph G;
+  if (build(n_edges, off, nodes, G)) return -1;
+  std::fill(out_h, out_h + 26, 0);
+  std::fill(out_3h, out_3h + 431, 0);
+  const int64_t E = (int64_t)G.e.size();
+  for (int64_t a = 0; a < n_rows; ++a)
+    if (rows[a] < 0 || rows[a] >= E) return -1;
+  auto before = [&](int64_t x, int64_t y) { return rank ? rank[x] < rank[y] : x < y; };
+  auto overlap = [&](int64_t x, int64_t y) {
+    const auto& s = G.e[x].size() <= G.e[y].size() ? G.e[x] : G.e[y];
+    const auto& o = G.e[x].size() <= G.e[y].size() ? G.eset[y] : G.eset[x];
+    int64_t c = 0;
+    for (int32_t v : s) c += o.count(v) ? 1 : 0;
+    return c;
+  };
+  // add (sign +1 / -1) the "as if open" term of centre c with leaves p, q
+  auto as_if_open = [&](int64_t c, int64_t p, int64_t q, int64_t wcp, int64_t wcq, int64_t sign,
+                        int64_t* h, int64_t* h3) {
+    const int64_t A = (int64_t)G.e[c].size();
+    if (wcp + wcq > A) return;
+    const std::array<int64_t, 7> r = {A - wcp - wcq, (int64_t)G.e[p].size() - wcp,
+                                      (int64_t)G.e[q].size() - wcq, wcp, 0, wcq, 0};
+    int hh, t3;
+    classify(r, theta, &hh, &t3);
+    h[hh - 1] += sign;
+    h3[t3 - 1] += sign;
+  };
+  auto row_body = [&](int32_t r, int64_t* h, int64_t* h3) {
+    const auto Nr = get_neighbors(G, r);
+    std::vector<std::pair<int32_t, int32_t>> N(Nr.begin(), Nr.end());
+    for (size_t x = 0; x < N.size(); ++x)
+      for (size_t y = x + 1; y < N.size(); ++y) {
+        const int32_t j = N[x].first, k = N[y].first;
+        const int64_t wrj = N[x].second, wrk = N[y].second;
+        as_if_open(r, j, k, wrj, wrk, +1, h, h3);
+        const int64_t wjk = overlap(j, k);
+        if (wjk == 0 || !(before(r, j) && before(r, k))) continue;
+        auto reg = regions(G, r, j, k, wrj, wjk, wrk);
+        int hh, t3;
+        classify(reg, theta, &hh, &t3);
+        h[hh - 1] += 1;
+        h3[t3 - 1] += 1;
+        as_if_open(r, j, k, wrj, wrk, -1, h, h3);
+        as_if_open(j, r, k, wrj, wjk, -1, h, h3);
+        as_if_open(k, r, j, wrk, wjk, -1, h, h3);
+      }
+  };
+  tables();
+  const int nt = threads > 1 ? threads : 1;
+  std::vector<std::vector<int64_t>> part(nt, std::vector<int64_t>(26 + 431, 0));
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1)
+#endif
+  for (int64_t a = 0; a < n_rows; ++a) {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    row_body(rows[a], part[tid].data(), part[tid].data() + 26);
+  }
+  for (int t = 0; t < nt; ++t) {
+    for (int q = 0; q < 26; ++q) out_h[q] += part[t][q];
+    for (int q = 0; q < 431; ++q) out_3h[q] += part[t][26 + q];
+  }
+  return 0;
+}
+
+}  // extern "C"

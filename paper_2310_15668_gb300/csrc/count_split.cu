@@ -1710,10 +1710,12 @@ __global__ void k_rows_by_kind(int64_t n, const int32_t* __restrict__ rows,
 }
 }  // namespace
 
-// The part of the split count that a set of rows contributes: open instances
-// centred at a row of the set, and closed instances whose first member in
-// the split's order (sparse rows by id, then dense rows by line degree and
-// id) is in the set.  Summed over all rows it is the exact count.
+// The share of a set of rows in the split count: the pairs of each row's
+// neighbours as if open (open-pair kernel, centres of the set only), and the
+// closed instances whose first member in the split's order (sparse rows by
+// id, then dense rows by line degree and id) is in the set, each with its
+// as-if-open terms taken off (triangle kernels, rows of the set only).
+// Summed over all rows it is the exact count.
 int count_split_rows(mochy_ctx* ctx, const int32_t* d_rows, int64_t n_rows,
                      unsigned long long* d_hist) {
   if (ctx->n_units != 1) return fail(MOCHY_E_INVALID, "row subsets need a lone hypergraph");

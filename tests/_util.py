@@ -101,3 +101,19 @@ def realise(pattern):
                 sets[who].add(nxt)
             nxt += 1
     return [frozenset(s) for s in sets], nxt
+
+
+def canonical_tuple(p):
+    """Smallest region tuple over the six relabellings of the three
+    hyperedges of a pattern given as states of regions (1)..(7)."""
+    member = [1, 2, 4, 3, 6, 5, 7]
+    region = {m: r for r, m in enumerate(member)}
+    best = None
+    for perm in itertools.permutations(range(3)):
+        q = [0] * 7
+        for r, m in enumerate(member):
+            m2 = sum(1 << perm[b] for b in range(3) if m & (1 << b))
+            q[region[m2]] = p[r]
+        q = tuple(q)
+        best = q if best is None or q < best else best
+    return best

@@ -18,11 +18,12 @@ and the 26 h-motif and 431 3h-motif counts must equal the oracle's as int64.
 The kernel's trace counters show that each path ran.
 
 The medium bench workload itself (100,000 nodes, 200,000 hyperedges,
-4.2e13 instances) is too large for the oracle to count whole; there the rows
-of a seeded sample are counted by the split kernel (mochy_count_exact_rows)
-and by the oracle under the same order of hyperedges, and the full count
-must satisfy open + 3 closed = sum_e C(|N_e|, 2) with line degrees from the
-oracle.
+4.2e13 instances) is too large for the oracle to count whole; there the
+shares of a seeded sample of rows (mochy_count_exact_rows: a row's neighbour
+pairs as if open, plus the closed instances it owns in the split order
+minus their as-if-open terms) must equal the oracle's shares under the same
+order, and the full count must satisfy open + 3 closed = sum_e C(|N_e|, 2)
+with line degrees from the oracle.
 """
 import numpy as np
 import pytest
@@ -127,9 +128,10 @@ def test_split_kernel_other_theta_on_multichunk_graph():
 
 @pytest.mark.parametrize("name", ["zipf6k", "zipf6k_clusters"])
 def test_split_rows_match_oracle_under_the_split_order(name):
-    """Row subsets of the split kernel equal the oracle's anchor subsets when
-    the oracle compares hyperedges in the split kernel's order; the parts of
-    a partition of all rows add up to the full count."""
+    """Row shares of the split kernel (pairs of a row's neighbours as if
+    open, plus the closed instances it owns in the split order minus their
+    as-if-open terms) equal the oracle's shares under the same order; the
+    parts of a partition of all rows add up to the full count."""
     n, off, nodes = _graph(name)
     thr = GRAPHS[name][1]
     deg = oracle.line_degrees(off, nodes)
@@ -145,7 +147,7 @@ def test_split_rows_match_oracle_under_the_split_order(name):
                                rng.choice(sparse, min(20, sparse.size), replace=False)])
         rows = rows.astype(np.int32)
         g = c.count_exact_rows(rows)
-        o = oracle.count_exact_ranked(off, nodes, rows, rank, threads=0)
+        o = oracle.count_split_rows(off, nodes, rows, rank, threads=0)
         assert np.array_equal(g[0], o[0]) and np.array_equal(g[1], o[1])
         parts = np.array_split(rng.permutation(e).astype(np.int32), 3)
         acc = sum(c.count_exact_rows(p)[1] for p in parts)
@@ -209,8 +211,8 @@ def test_medium_rows_match_oracle(medium):
         B.mochy_trace(c.h, 2)
         g = c.count_exact_rows(rows)
         tr = B.mochy_trace_read(c.h)
-    o = oracle.count_exact_ranked(off, nodes, rows, rank, threads=0)
+    o = oracle.count_split_rows(off, nodes, rows, rank, threads=0)
     assert np.array_equal(g[1], o[1])
     assert np.array_equal(g[0], o[0])
     assert tr["dense_rows_counted"] == 42 and tr["slots_evicted"] > 0
-    assert g[0].sum() > 0
+    assert g[1].any()

@@ -198,3 +198,63 @@ def test_line_degrees_from_incidence_lists():
         ld = oracle.line_degrees(off, nodes, threads=3)
         assert np.array_equal(ld, deg)
         assert int(ld.sum()) == 2 * nw and int(ld.max()) == md
+
+
+def _split_share_brute(sets, r, rank, theta=1):
+    """A row's share when open instances are counted per centre from all its
+    neighbour pairs: every pair {p, q} of neighbours of r classified as if
+    open at r (regions of an open instance from the overlaps with r, when
+    they fit in e_r), plus, for a closed instance whose lowest-ranked member
+    is r, its pattern minus its as-if-open pattern at each of its three
+    centres.  From the node sets, {canonical tuple: count}."""
+    def state(c):
+        return 0 if c == 0 else (1 if c <= theta else 2)
+
+    def as_if_open(c, p, q):
+        C, P, Q = sets[c], sets[p], sets[q]
+        wcp, wcq = len(C & P), len(C & Q)
+        if wcp + wcq > len(C):
+            return None
+        regs = (len(C) - wcp - wcq, len(P) - wcp, len(Q) - wcq, wcp, 0, wcq, 0)
+        return _util.canonical_tuple(tuple(state(v) for v in regs))
+
+    out = {}
+
+    def add(key, v):
+        if key is not None:
+            out[key] = out.get(key, 0) + v
+
+    nbrs = [i for i in range(len(sets)) if i != r and sets[i] & sets[r]]
+    for a in range(len(nbrs)):
+        for b in range(a + 1, len(nbrs)):
+            j, k = nbrs[a], nbrs[b]
+            add(as_if_open(r, j, k), 1)
+            if sets[j] & sets[k] and rank[r] < rank[j] and rank[r] < rank[k]:
+                add(_util.canonical_of_sets(sets[r], sets[j], sets[k], theta), 1)
+                add(as_if_open(r, j, k), -1)
+                add(as_if_open(j, r, k), -1)
+                add(as_if_open(k, r, j), -1)
+    return {key: v for key, v in out.items() if v}
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_split_row_shares_match_brute_force(T, seed):
+    sets = _util.micro_graph(720 + seed, n_nodes=11, n_edges=22, s_max=5)
+    off, nodes = _util.csr_from_sets(sets)
+    rank = np.random.default_rng(seed).permutation(len(sets)).astype(np.int64)
+    for r in range(len(sets)):
+        _, h3 = oracle.count_split_rows(off, nodes, [r], rank)
+        assert _util.counts_by_tuple(T["t_pattern"], h3) == _split_share_brute(sets, r, rank)
+
+
+def test_split_row_shares_sum_to_the_exact_count():
+    spec = synth.HypergraphSpec(400, 900, 2, 12, "powerlaw", 2.5, "zipf", 0.8, seed=9)
+    off, nodes = synth.generate(spec)
+    h, h3 = oracle.count_exact(off, nodes)
+    e = off.size - 1
+    for seed in range(2):
+        rank = np.random.default_rng(seed).permutation(e).astype(np.int64)
+        parts = np.array_split(np.random.default_rng(seed + 7).permutation(e).astype(np.int32), 3)
+        acc_h = sum(oracle.count_split_rows(off, nodes, p, rank, threads=3)[0] for p in parts)
+        acc_3h = sum(oracle.count_split_rows(off, nodes, p, rank, threads=3)[1] for p in parts)
+        assert np.array_equal(acc_h, h) and np.array_equal(acc_3h, h3)

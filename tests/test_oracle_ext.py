@@ -100,19 +100,7 @@ def test_4h_counts_merge_into_3h_counts():
         assert got == want
 
 
-def _canon(p):
-    """Smallest region tuple over the six relabellings of the hyperedges."""
-    member = [1, 2, 4, 3, 6, 5, 7]
-    region = {m: r for r, m in enumerate(member)}
-    best = None
-    for perm in itertools.permutations(range(3)):
-        q = [0] * 7
-        for r, m in enumerate(member):
-            m2 = sum(1 << perm[b] for b in range(3) if m & (1 << b))
-            q[region[m2]] = p[r]
-        q = tuple(q)
-        best = q if best is None or q < best else best
-    return best
+_canon = _util.canonical_tuple
 
 
 def _radial_brute(sets, n_nodes):
