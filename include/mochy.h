@@ -155,6 +155,24 @@ int mochy_count_exact_subset(mochy_ctx* ctx, const int32_t* h_anchors,
 int mochy_count_exact_rows(mochy_ctx* ctx, const int32_t* h_rows, int64_t n_rows,
                            int64_t out_h[MOCHY_N_H], int64_t out_3h[MOCHY_N_3H]);
 
+/* Measured choice of the split kernel's dense threshold (the line degree
+ * from which a row's overlaps are kept as bit-planes): for each of the
+ * n_candidates thresholds (host int32, each >= 2; with n_candidates = 0 the
+ * tuner's model choice m and m/4, m/2, 2m, 4m) the split structures are
+ * built and the split count of one seeded sample of rows (each row kept
+ * with probability sample_fraction by a SplitMix64 hash of (seed, row)) is
+ * timed with CUDA events on the context's stream.  The fastest threshold
+ * becomes the context's dense threshold for the following counts and is
+ * written to *best (may be NULL); tried and ms (may be NULL; n_candidates
+ * entries, 5 for the default list) receive each candidate and its time in
+ * milliseconds, -1 where its structures did not fit (device memory or the
+ * kernels' limits).  The
+ * paper has no counterpart (its exact count has no such threshold).  Needs
+ * mochy_project; MOCHY_E_INVALID for the scan kernel or a batch. */
+int mochy_tune_dense_threshold(mochy_ctx* ctx, const int32_t* candidates, int32_t n_candidates,
+                               double sample_fraction, uint64_t seed, int32_t* best,
+                               int32_t* tried, double* ms);
+
 /* Hyperedge profiles (Section 3.1, "Hyperedge Profile (HP)"; Section 4.1
  * for their 3h-motif form): hp_h[e * 26 + t - 1] is the number of instances
  * of h-motif t that include hyperedge e, hp_3h[e * 431 + t - 1] the same for

@@ -32,6 +32,7 @@ EXPORTS = [
     "mochy_count_sampled_noalloc", "mochy_profile_batch", "mochy_server_create",
     "mochy_hyperedge_profile", "mochy_star_node_profile", "mochy_radial_node_profile",
     "mochy_count_kh", "mochy_kh_pattern", "mochy_enumerate", "mochy_count_sampled_onthefly",
+    "mochy_tune_dense_threshold",
     "mochy_server_submit", "mochy_server_poll", "mochy_server_stats", "mochy_server_destroy",
 ]
 MOCHY_REQ_EXACT, MOCHY_REQ_SAMPLED, MOCHY_REQ_PROFILE = 1, 2, 3
@@ -154,6 +155,8 @@ def load_library(path: str = LIB_PATH):
             lib.mochy_count_kh.argtypes = [vp, i32, vp, vp, vp, i64, vp]
             lib.mochy_kh_pattern.argtypes = [vp, i32, i32, vp]
             lib.mochy_enumerate.argtypes = [vp, i64, vp, vp]
+            lib.mochy_tune_dense_threshold.argtypes = [vp, vp, i32, ctypes.c_double,
+                                                       ctypes.c_uint64, vp, vp, vp]
             lib.mochy_count_sampled_onthefly.argtypes = [vp, i64, ctypes.c_uint64, i64, vp, vp,
                                                          vp, vp, vp]
             lib.mochy_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(mochy_config),
@@ -356,6 +359,21 @@ def mochy_count_sampled_onthefly(ctx: int, samples: int, seed: int, budget: int 
                                                         _p(r3), _p(eh), _p(e3), _p(nw)),
            "mochy_count_sampled_onthefly")
     return rh, r3, eh, e3, int(nw[0])
+
+
+def mochy_tune_dense_threshold(ctx: int, candidates=(), sample_fraction: float = 0.02,
+                               seed: int = 1):
+    """Measured dense threshold: (best, [(candidate, ms)]); the context
+    keeps the best for its following counts."""
+    c = np.ascontiguousarray(candidates, dtype=np.int32)
+    n = c.size if c.size else 5
+    ms = np.zeros(n, np.float64)
+    tried = np.zeros(n, np.int32)
+    best = np.zeros(1, np.int32)
+    _check(load_library().mochy_tune_dense_threshold(
+        ctx, _p(c) if c.size else None, int(c.size), float(sample_fraction), seed, _p(best),
+        _p(tried), _p(ms)), "mochy_tune_dense_threshold")
+    return int(best[0]), list(zip(tried.tolist(), ms.tolist()))
 
 
 def mochy_kh_pattern(ctx: int, k: int, motif_id: int) -> np.ndarray:

@@ -438,6 +438,24 @@ int mochy_count_exact_rows(mochy_ctx* ctx, const int32_t* h_rows, int64_t n, int
   return rc;
 }
 
+int mochy_tune_dense_threshold(mochy_ctx* ctx, const int32_t* candidates, int32_t n_candidates,
+                               double sample_fraction, uint64_t seed, int32_t* best,
+                               int32_t* tried, double* ms) {
+  if (!ctx) return fail(MOCHY_E_INVALID, "null context");
+  if (n_candidates < 0 || (n_candidates > 0 && !candidates))
+    return fail(MOCHY_E_INVALID, "bad candidates");
+  for (int32_t c = 0; c < n_candidates; ++c)
+    if (candidates[c] < 2) return fail(MOCHY_E_INVALID, "thresholds must be at least 2");
+  if (!(sample_fraction > 0.0 && sample_fraction <= 1.0))
+    return fail(MOCHY_E_INVALID, "sample_fraction must lie in (0, 1]");
+  if (!ctx->projected) return fail(MOCHY_E_NOT_PROJECTED, "call mochy_project first");
+  if (ctx->exact_kernel != 0 || ctx->n_units != 1)
+    return fail(MOCHY_E_INVALID, "the tuner needs the split kernel on a lone hypergraph");
+  MOCHY_TRY(device_guard(ctx));
+  return tune_dense_threshold(ctx, candidates, n_candidates, sample_fraction, seed, best, tried,
+                              ms);
+}
+
 int mochy_hyperedge_profile(mochy_ctx* ctx, int64_t* hp_h, int64_t* hp_3h) {
   if (!ctx) return fail(MOCHY_E_INVALID, "null context");
   MOCHY_TRY(device_guard(ctx));

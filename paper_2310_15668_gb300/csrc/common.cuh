@@ -229,6 +229,10 @@ void release_onthefly(mochy_ctx* ctx);                                // onthefl
 int enumerate_instances(mochy_ctx* ctx, int64_t cap, int32_t* d_out,
                         unsigned long long* d_cursor);                // extensions.cu
 int prepare_split(mochy_ctx* ctx);                                    // count_split.cu
+int choose_dense_threshold(mochy_ctx* ctx);                           // tune.cu
+int tune_dense_threshold(mochy_ctx* ctx, const int32_t* cand, int32_t n_cand, double fraction,
+                         uint64_t seed, int32_t* best, int32_t* tried,
+                         double* ms);                                 // tune.cu
 void release_split(mochy_ctx* ctx);                                   // count_split.cu
 int count_sampled(mochy_ctx* ctx, int method, int64_t samples, uint64_t seed,
                   unsigned long long* d_hist);                        // sample.cu

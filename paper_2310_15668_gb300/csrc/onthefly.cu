@@ -96,6 +96,8 @@ struct OtfWarp {
   int32_t ln[kOtfNodes];          // list node
   int32_t lpart[kOtfNodes];
   int64_t lpos[kOtfNodes], lend[kOtfNodes];
+  int64_t lnext[kOtfNodes];       // id of the list's next entry (INT64_MAX when done)
+  uint32_t lw[32];                // one list's entries of a chunk, as word masks
   int32_t nh, nl;
   uint32_t table[kOtfKeys];
   uint32_t dirty[kOtfKeys / 32];
@@ -142,8 +144,10 @@ __device__ void split_nodes(const OtfArgs& g, OtfWarp& me, int A, int B, bool pa
         me.ln[q] = v;
         me.lpart[q] = part;
         const int64_t vb = g.voff[v], ve = g.voff[v + 1];
-        me.lpos[q] = lower_bound_i32(g.vedge, vb, ve, from);
+        const int64_t ps = lower_bound_i32(g.vedge, vb, ve, from);
+        me.lpos[q] = ps;
         me.lend[q] = ve;
+        me.lnext[q] = ps < ve ? (int64_t)g.vedge[ps] : INT64_MAX;
       }
       __syncwarp();
       if (lane == 0) {
@@ -177,28 +181,39 @@ __device__ __forceinline__ void gather_chunk(const OtfArgs& g, OtfWarp& me, int6
     else if (p == 1) slice_add(s.c[1][0], s.c[1][1], s.c[1][2], s.c[1][3], word);
     else slice_add(s.c[2][0], s.c[2][1], s.c[2][2], s.c[2][3], word);
   }
+  // list nodes: a list's entries are distinct hyperedges, so its entries in
+  // this chunk are one mask per word (shared-memory OR), added once per list
   const int64_t hi = (w0 + 32) * 32;
   for (int q = 0; q < nl; ++q) {
+    if (me.lnext[q] >= hi) continue;   // uniform: nothing of this list here
     const int p = me.lpart[q];
     while (true) {
       const int64_t pos = me.lpos[q], end = me.lend[q];
       const int64_t e = pos + lane < end ? (int64_t)g.vedge[pos + lane] : INT64_MAX;
-      const int nin = __popc(__ballot_sync(0xffffffffu, e < hi));
-      for (int jj = 0; jj < nin; ++jj) {
-        const int64_t f = __shfl_sync(0xffffffffu, e, jj);
-        if ((f >> 5) == w) {
-          const uint32_t m = 1u << (f & 31);
-          if (p == 0) slice_add(s.c[0][0], s.c[0][1], s.c[0][2], s.c[0][3], m);
-          else if (p == 1) slice_add(s.c[1][0], s.c[1][1], s.c[1][2], s.c[1][3], m);
-          else slice_add(s.c[2][0], s.c[2][1], s.c[2][2], s.c[2][3], m);
-        }
-      }
+      const bool in = e < hi;
+      const int nin = __popc(__ballot_sync(0xffffffffu, in));
+      if (in) atomicOr(&me.lw[(e >> 5) - w0], 1u << (e & 31));
       n_entries += (unsigned long long)nin;
+      const int64_t nx = __shfl_sync(0xffffffffu, e, nin & 31);
       __syncwarp();
-      if (lane == 0) me.lpos[q] = pos + nin;
+      if (lane == 0) {
+        me.lpos[q] = pos + nin;
+        me.lnext[q] = nin < 32 ? nx : INT64_MAX;
+      }
       __syncwarp();
       if (nin < 32) break;
+      if (me.lpos[q] >= end) {
+        if (lane == 0) me.lnext[q] = INT64_MAX;
+        __syncwarp();
+        break;
+      }
     }
+    const uint32_t m = me.lw[lane];
+    me.lw[lane] = 0u;
+    __syncwarp();
+    if (p == 0) slice_add(s.c[0][0], s.c[0][1], s.c[0][2], s.c[0][3], m);
+    else if (p == 1) slice_add(s.c[1][0], s.c[1][1], s.c[1][2], s.c[1][3], m);
+    else slice_add(s.c[2][0], s.c[2][1], s.c[2][2], s.c[2][3], m);
   }
 }
 
@@ -208,7 +223,7 @@ __device__ __forceinline__ int64_t next_list_word(const OtfArgs& g, const OtfWar
   const int lane = threadIdx.x & 31;
   int64_t best = g.W;
   for (int q = lane; q < me.nl; q += 32)
-    if (me.lpos[q] < me.lend[q]) best = min(best, (int64_t)g.vedge[me.lpos[q]] >> 5);
+    if (me.lnext[q] != INT64_MAX) best = min(best, me.lnext[q] >> 5);
   for (int d = 16; d; d >>= 1) best = min(best, (int64_t)__shfl_xor_sync(0xffffffffu, best, d));
   return best;
 }
@@ -224,6 +239,8 @@ __global__ void __launch_bounds__(kOtfThreads) k_otf_degrees(OtfArgs g) {
   OtfWarp& me = ((OtfWarp*)smem)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * kOtfWarps;
+  me.lw[lane] = 0u;
+  __syncwarp();
   for (int64_t i = (int64_t)blockIdx.x * kOtfWarps + (threadIdx.x >> 5); i < g.n_edges;
        i += nwarps) {
     const int A = (int)(g.eoff[i + 1] - g.eoff[i]);
@@ -283,6 +300,15 @@ __device__ __forceinline__ void exact_overlaps(const int32_t* a, int A, const in
   }
 }
 
+// Popcounted bins for theta = 1: (xa, xb, xt, effective size).  The motif
+// depends on |e_k| only through min(|e_k|, xa + xb + 2 xt + 2), so the last
+// size class of each combination stands for every larger size.
+__constant__ int kPopBin[13][4] = {
+    {0, 0, 1, 1}, {0, 0, 1, 2}, {0, 0, 1, 3}, {0, 0, 1, 4},   // closed through e_i & e_j only
+    {1, 0, 0, 1}, {1, 0, 0, 2}, {1, 0, 0, 3},                 // open, centre e_i
+    {0, 1, 0, 1}, {0, 1, 0, 2}, {0, 1, 0, 3},                 // open, centre e_j
+    {1, 1, 0, 2}, {1, 1, 0, 3}, {1, 1, 0, 4}};                // closed, empty triple region
+
 // One warp per drawn hyperwedge (work queue over the samples).
 // Shared: hist[432] | lut[2192] | OtfWarp[kOtfWarps]
 __global__ void __launch_bounds__(kOtfThreads) k_otf_sample(OtfArgs g) {
@@ -295,6 +321,7 @@ __global__ void __launch_bounds__(kOtfThreads) k_otf_sample(OtfArgs g) {
   for (int q = threadIdx.x; q < 2187; q += kOtfThreads) lut[q] = g.lut3[q];
   for (int q = lane; q < kOtfKeys; q += 32) me.table[q] = 0u;
   me.dirty[lane] = 0u;
+  me.lw[lane] = 0u;
   __syncthreads();
   const int theta = g.theta;
   unsigned long long st_cand = 0, st_words = 0, st_ent = 0, st_exact = 0;
@@ -367,6 +394,11 @@ __global__ void __launch_bounds__(kOtfThreads) k_otf_sample(OtfArgs g) {
     for (int d = 16; d; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
     // classification of N_i u N_j \ {i, j}
     const bool scan_all = me.nh > 0;
+    // theta = 1: per-lane counts of the four commonest (xa, xb, xt) by
+    // size class (see kPopBin below); the others go through the table
+    uint32_t bins[13];
+#pragma unroll
+    for (int b = 0; b < 13; ++b) bins[b] = 0u;
     int64_t w0 = scan_all ? 0 : next_list_word(g, me);
     while (w0 < g.W) {
       Slices s;
@@ -377,14 +409,41 @@ __global__ void __launch_bounds__(kOtfThreads) k_otf_sample(OtfArgs g) {
       if (w == (i >> 5)) m &= ~(1u << (i & 31));
       if (w == (j >> 5)) m &= ~(1u << (j & 31));
       st_words += inr ? 1 : 0;
+      st_cand += __popc(m);
       const uint32_t p0 = inr ? __ldg(&g.sbits[w]) : 0u, p1 = inr ? __ldg(&g.sbits[g.W + w]) : 0u;
       const uint32_t p2 = inr ? __ldg(&g.sbits[2 * g.W + w]) : 0u;
       const uint32_t p3 = inr ? __ldg(&g.sbits[3 * g.W + w]) : 0u;
       const uint32_t ovf = s.c[0][3] | s.c[1][3] | s.c[2][3];
-      // candidates, 32 at a time over the whole warp: lane l takes the l-th
-      // remaining candidate of this chunk
+      if (theta == 1) {
+        const uint32_t az = ~(s.c[0][0] | s.c[0][1] | s.c[0][2] | s.c[0][3]);
+        const uint32_t a1 = s.c[0][0] & ~(s.c[0][1] | s.c[0][2] | s.c[0][3]);
+        const uint32_t bz = ~(s.c[1][0] | s.c[1][1] | s.c[1][2] | s.c[1][3]);
+        const uint32_t b1 = s.c[1][0] & ~(s.c[1][1] | s.c[1][2] | s.c[1][3]);
+        const uint32_t tz = ~(s.c[2][0] | s.c[2][1] | s.c[2][2] | s.c[2][3]);
+        const uint32_t t1 = s.c[2][0] & ~(s.c[2][1] | s.c[2][2] | s.c[2][3]);
+        const uint32_t c001 = m & az & bz & t1, c100 = m & a1 & bz & tz;
+        const uint32_t c010 = m & az & b1 & tz, c110 = m & a1 & b1 & tz;
+        const uint32_t hi4 = p2 | p3;
+        const uint32_t e1 = ~hi4 & ~p1 & p0, e2 = ~hi4 & p1 & ~p0, e3 = ~hi4 & p1 & p0;
+        const uint32_t ge3 = e3 | hi4;
+        bins[0] += __popc(c001 & e1);
+        bins[1] += __popc(c001 & e2);
+        bins[2] += __popc(c001 & e3);
+        bins[3] += __popc(c001 & hi4);
+        bins[4] += __popc(c100 & e1);
+        bins[5] += __popc(c100 & e2);
+        bins[6] += __popc(c100 & ge3);
+        bins[7] += __popc(c010 & e1);
+        bins[8] += __popc(c010 & e2);
+        bins[9] += __popc(c010 & ge3);
+        bins[10] += __popc(c110 & e2);
+        bins[11] += __popc(c110 & e3);
+        bins[12] += __popc(c110 & hi4);
+        m &= ~(c001 | c100 | c010 | c110);
+      }
+      // remaining candidates, 32 at a time over the whole warp: lane l takes
+      // the l-th remaining candidate of this chunk
       const int rc = __popc(m);
-      st_cand += rc;
       int incl = rc;
       for (int d = 1; d < 32; d <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, incl, d);
@@ -439,6 +498,21 @@ __global__ void __launch_bounds__(kOtfThreads) k_otf_sample(OtfArgs g) {
         }
       }
       w0 = scan_all ? w0 + 32 : max(w0 + 32, next_list_word(g, me));
+    }
+    // the popcounted bins: (xa, xb, xt) and the size they stand for
+    if (theta == 1) {
+      uint32_t mine = 0u;
+#pragma unroll
+      for (int b = 0; b < 13; ++b) {
+        const uint32_t v = __reduce_add_sync(0xffffffffu, bins[b]);
+        if (lane == b) mine = v;
+      }
+      if (lane < 13 && mine) {
+        const int xa = kPopBin[lane][0], xb = kPopBin[lane][1], xt = kPopBin[lane][2];
+        const int ce = kPopBin[lane][3];
+        atomicAdd(&hist[lut[ternary_code(A, B, ce, x, xb + xt, xa + xt, xt, 1)]],
+                  (unsigned long long)mine);
+      }
     }
     // the groups of this hyperwedge, classified once each
     __syncwarp();

@@ -82,3 +82,92 @@ int choose_dense_threshold(mochy_ctx* ctx) {
 }
 
 }  // namespace mochy
+
+namespace mochy {
+
+int count_split_rows(mochy_ctx* ctx, const int32_t* d_rows, int64_t n_rows,
+                     unsigned long long* d_hist);   // count_split.cu
+
+// Measured choice of the dense threshold: for each candidate threshold the
+// split structures are built and the split count of one seeded sample of
+// rows (the same rows for every candidate) is timed with CUDA events on the
+// context's stream; the fastest candidate is kept as the context's
+// threshold.  A candidate whose structures do not fit the device memory or
+// the kernels' limits is skipped (its time is reported as -1).
+int tune_dense_threshold(mochy_ctx* ctx, const int32_t* cand, int32_t n_cand, double fraction,
+                         uint64_t seed, int32_t* best_out, int32_t* tried_out, double* ms_out) {
+  const int64_t E = ctx->n_edges;
+  std::vector<int32_t> cs(cand, cand + n_cand);
+  if (cs.empty()) {
+    ctx->dense_thr = 0;
+    const int model = choose_dense_threshold(ctx);
+    if (model < 0) return model;
+    for (int f : {4, 2}) cs.push_back(std::max(32, model / f));
+    cs.push_back(model);
+    for (int f : {2, 4}) cs.push_back(model * f);
+  }
+  // the sample: rows whose 64-bit hash of (seed, row) falls below fraction
+  std::vector<int32_t> rows;
+  const uint64_t cut = (uint64_t)(std::min(std::max(fraction, 0.0), 1.0) * 18446744073709551615.0);
+  for (int64_t r = 0; r < E; ++r) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(r + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    if (z <= cut) rows.push_back((int32_t)r);
+  }
+  if (rows.empty()) rows.push_back(0);
+  void* d = nullptr;
+  MOCHY_TRY(dev_alloc(ctx, &d, rows.size() * 4));
+  int rc = MOCHY_OK;
+  if (cudaMemcpyAsync(d, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, ctx->stream) !=
+      cudaSuccess)
+    rc = fail(MOCHY_E_CUDA, "tuner row copy failed");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int32_t saved = ctx->dense_thr;
+  int32_t best = -1;
+  double best_ms = 0.0;
+  for (size_t c = 0; c < cs.size() && rc == MOCHY_OK; ++c) {
+    release_split(ctx);
+    ctx->dense_thr = cs[c];
+    double ms = -1.0;
+    if (prepare_split(ctx) == MOCHY_OK) {
+      cudaEventRecord(e0, ctx->stream);
+      const int r2 = count_split_rows(ctx, (const int32_t*)d, (int64_t)rows.size(), ctx->hist);
+      cudaEventRecord(e1, ctx->stream);
+      if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        rc = fail(MOCHY_E_CUDA, "tuner count failed");
+      } else if (r2 == MOCHY_OK) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms = t;
+        if (best < 0 || ms < best_ms) {
+          best = cs[c];
+          best_ms = ms;
+        }
+      }
+    }
+    if (ms_out) ms_out[c] = ms;
+    if (tried_out) tried_out[c] = cs[c];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  release_split(ctx);
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(ctx, d, rows.size() * 4);
+  if (rc != MOCHY_OK) {
+    ctx->dense_thr = saved;
+    return rc;
+  }
+  if (best < 0) {
+    ctx->dense_thr = saved;
+    return fail(MOCHY_E_UNSUPPORTED, "no candidate threshold fits");
+  }
+  ctx->dense_thr = best;
+  if (best_out) *best_out = best;
+  return MOCHY_OK;
+}
+
+}  // namespace mochy

@@ -216,3 +216,21 @@ def test_medium_rows_match_oracle(medium):
     assert np.array_equal(g[0], o[0])
     assert tr["dense_rows_counted"] == 42 and tr["slots_evicted"] > 0
     assert g[1].any()
+
+
+def test_measured_tuner_keeps_the_fastest_threshold_and_counts_stay_exact():
+    n, off, nodes = _graph("zipf6k")
+    with B.Context() as c:
+        c.load(n, off, nodes)
+        c.project()
+        best, tried = B.mochy_tune_dense_threshold(c.h, [16, 32, 64, 128], 0.05, 3)
+        assert [t for t, _ in tried] == [16, 32, 64, 128]
+        assert all(ms > 0 for _, ms in tried)
+        assert best == min(tried, key=lambda x: x[1])[0]
+        B.mochy_trace(c.h, 1)
+        h, h3 = c.count_exact()
+        assert B.mochy_trace_read(c.h)["dense_threshold"] == best
+        best2, tried2 = B.mochy_tune_dense_threshold(c.h)        # the model's five
+        assert len(tried2) == 5 and best2 in [t for t, _ in tried2]
+    oh, o3 = _oracle_counts("zipf6k")
+    assert np.array_equal(h3, o3) and np.array_equal(h, oh)
