@@ -289,12 +289,16 @@ __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
 // node lists.
 // Shared layout: hist | lut | anodes[64] | WarpScratch[kDWarps]
 // ---------------------------------------------------------------------------
-constexpr int kDThreads = 256;
+// 4 warps per CTA and 5 CTAs per SM (96 registers, 42 KB of shared memory
+// per CTA): 20 resident warps per SM; measured on the medium workload
+// against 8-warp CTAs at 2 per SM (16 warps, 125 registers; 24.0 s) and at 3
+// per SM (80 registers, spilling; 27.3 s): 22.8 s
+constexpr int kDThreads = 128;
 constexpr int kDWarps = kDThreads / 32;
 constexpr int kCeff = 16;          // effective sizes kept in the table
 constexpr int kCombo = 64;         // (xa, xb, xt) with each count below 4
 
-constexpr int kLight = 512;        // merged light-node entries per hyperwedge
+constexpr int kLight = 256;        // merged light-node entries per hyperwedge (a power of two)
 constexpr int kSlots = 8;          // per-warp signature slots of popcounted bins (theta = 1)
 constexpr uint32_t kSlotFlush = 1024;   // hyperwedges per slot before it is flushed
 
@@ -417,7 +421,7 @@ __device__ __forceinline__ void flush_slot(WS& me, int q, unsigned long long* hi
 }
 
 template <bool kTheta1, bool kSeg>
-__global__ void __launch_bounds__(kDThreads) k_dense_triangles(SplitArgs g) {
+__global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* hist = (unsigned long long*)smem;
   uint16_t* lut = (uint16_t*)(hist + 432);
