@@ -155,6 +155,30 @@ def reduce_over_ranks(ms: float, units: float, world_size: int, device: str):
     return float(t.item()), float(u.item())
 
 
+def partition_rows(deg, world_size: int):
+    """Rows of one hypergraph dealt to ranks for the row-sharded count: rows in
+    decreasing estimated work |N_e|^2 (pairs of neighbours), dealt in snake
+    order (0, 1, .., n-1, n-1, .., 0, ...), so every rank gets a similar share
+    of the heavy rows.  Returns one int32 array of rows per rank."""
+    deg = np.asarray(deg, dtype=np.int64)
+    order = np.lexsort((np.arange(deg.size), -(deg * deg)))
+    pos = np.arange(order.size)
+    lap, k = pos // world_size, pos % world_size
+    owner = np.where(lap % 2 == 0, k, world_size - 1 - k)
+    return [np.sort(order[owner == r]).astype(np.int32) for r in range(world_size)]
+
+
+def reduce_counts(counts, world_size: int, device: str):
+    """Sum of every rank's int64 motif histogram (the row-sharded count's one
+    exchange; shares may be negative, the sum is the exact count)."""
+    import torch
+    t = torch.as_tensor(np.ascontiguousarray(counts, dtype=np.int64), device=device)
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t)
+    return t.cpu().numpy()
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -411,7 +435,9 @@ def run_gpu(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2310_15668_gb300 import binding as B, synth
-    spec = _spec(args.workload, rank)
+    # weak scaling: every rank its own hypergraph; --shard-rows: one
+    # hypergraph, its rows shared out (strong scaling)
+    spec = _spec(args.workload, 0 if args.shard_rows else rank)
     off, nodes = synth.generate(spec)
     d_off = torch.from_numpy(off).cuda()
     d_nodes = torch.from_numpy(nodes).cuda()
@@ -419,12 +445,24 @@ def run_gpu(args):
     stream = torch.cuda.ExternalStream(ctx.stream, device=local)
     instances = 0
 
+    shard = args.shard_rows and ws > 1
+    my_rows = None
+
     def step(trace=False):
-        nonlocal instances
+        nonlocal instances, my_rows
         B.mochy_load_device(ctx.h, spec.n_nodes, off.size - 1, d_off.data_ptr(),
                             d_nodes.data_ptr())
         ctx.project()
-        h, h3 = ctx.count_exact()
+        if shard:
+            # one hypergraph, rows dealt to ranks; the share of each rank's
+            # rows summed over ranks is the exact count
+            if my_rows is None:
+                my_rows = partition_rows(ctx.line_degrees(), ws)[rank]
+            h, h3 = ctx.count_exact_rows(my_rows)
+            both = reduce_counts(np.concatenate([h, h3]), ws, "cuda")
+            h, h3 = both[:26], both[26:]
+        else:
+            h, h3 = ctx.count_exact()
         instances = int(h.sum())
         return h, h3
 
@@ -449,7 +487,10 @@ def run_gpu(args):
     launches = B.mochy_kernel_launches() - launches0
     ms = start.elapsed_time(end)
     B.mochy_trace(ctx.h, 0)
-    ms_max, total_units = reduce_over_ranks(ms, float(instances) * args.steps, ws, "cuda")
+    units_here = float(instances) * args.steps
+    if shard and rank != 0:
+        units_here = 0.0                     # the one hypergraph is counted once
+    ms_max, total_units = reduce_over_ranks(ms, units_here, ws, "cuda")
     value = total_units / (ms_max / 1000.0)
 
     # kernel statistics (scanned words) from one more, untimed step at trace level 2
@@ -468,7 +509,11 @@ def run_gpu(args):
         for _ in range(args.e2e_steps):
             ctx.load(spec.n_nodes, p_off, p_nodes)
             ctx.project()
-            h, _ = ctx.count_exact()
+            if shard:
+                h, h3 = ctx.count_exact_rows(my_rows)
+                h = reduce_counts(np.concatenate([h, h3]), ws, "cuda")[:26]
+            else:
+                h, _ = ctx.count_exact()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
         e2e = {"value": float(h.sum()) * args.e2e_steps / dt, "unit": UNIT,
@@ -521,10 +566,13 @@ def run_gpu(args):
         serving = _serving_measure(args)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
             "config": {"workload": _workload_name(spec), "triples_per_step": instances,
                        "l2": "inputs larger than L2 (line graph of 30 GB per step)",
-                       "parallelism": f"independent hypergraph per rank x{ws}"},
+                       "parallelism": (f"rows of one hypergraph over {ws} ranks, one all-reduce "
+                                       f"of the 457 int64 bins" if shard else
+                                       f"independent hypergraph per rank x{ws}")},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk.summary(), "phases_ms": avg, "trace": st, "sampled": sampled,
             "onthefly": onthefly, "batch": batch, "serving": serving}
@@ -547,6 +595,8 @@ def main():
     ap.add_argument("--sampled-r", type=int, default=2_000_000,
                     help="MoCHy-A+ samples of the candidates/s line (0: skip)")
     ap.add_argument("--sampled-steps", type=int, default=3)
+    ap.add_argument("--shard-rows", action="store_true",
+                    help="with several ranks: count one hypergraph with its rows shared out")
     ap.add_argument("--onthefly-r", type=int, default=2_000_000,
                     help="MoCHy-A+ draws on the large workload without a line graph (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=1)

@@ -45,3 +45,37 @@ def test_max_time_and_summed_work_over_two_ranks():
 def test_single_rank_is_unchanged():
     import bench
     assert bench.reduce_over_ranks(5.0, 7.0, 1, "cpu") == (5.0, 7.0)
+
+
+def test_row_partition_covers_every_row_once_and_balances_work():
+    import numpy as np
+    import bench
+    deg = np.random.default_rng(3).zipf(1.6, size=5000).clip(0, 50_000)
+    for ws in (1, 2, 3, 8):
+        parts = bench.partition_rows(deg, ws)
+        allr = np.concatenate(parts)
+        assert np.array_equal(np.sort(allr), np.arange(deg.size))
+        work = [float((deg[p].astype(float) ** 2).sum()) for p in parts]
+        assert max(work) <= 1.25 * (sum(work) / ws) + float(deg.max()) ** 2
+
+
+def _share_main(rank, port, out):
+    import numpy as np
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    import bench
+    # two ranks' shares of one count, with negative entries as the split
+    # decomposition gives them
+    share = [np.array([5, -3, 2**40, 0], np.int64), np.array([1, 4, 7, -2], np.int64)][rank]
+    out[rank] = bench.reduce_counts(share, 2, "cpu").tolist()
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_row_shares_sum_over_two_ranks():
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_share_main, args=(port, out), nprocs=2, join=True)
+        res = dict(out)
+    assert res[0] == res[1] == [6, 1, 2**40 + 7, -2]
