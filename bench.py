@@ -333,13 +333,15 @@ def _onthefly_measure(args):
                                              "otf_exact", "otf_bitmaps")}}
 
 
-def _batch_measure(args):
+def _batch_measure(args, lo=None, hi=None):
     """CPs/s of the batched profile against one profile call per hypergraph."""
     from paper_2310_15668_gb300 import binding as B, synth
     G, R = args.batch_graphs, args.batch_copies
+    lo = args.batch_lo if lo is None else lo
+    hi = args.batch_hi if hi is None else hi
     gs = []
     for i in range(G):
-        s = synth.batch_spec(4, i, args.batch_lo, args.batch_hi)
+        s = synth.batch_spec(4, i, lo, hi)
         off, nodes = synth.generate(s)
         gs.append((s.n_nodes, off, nodes))
     seeds = [1000 + g for g in range(G)]
@@ -361,8 +363,8 @@ def _batch_measure(args):
     return {"metric": "CPs/s (significance + characteristic profile)",
             "value": G / t_batch, "one_at_a_time": G / t_one, "speedup": t_one / t_batch,
             "identical_counts_and_cps": bool(same),
-            "config": {"workload": f"{G} hypergraphs, E log-uniform in [{args.batch_lo}, "
-                                   f"{args.batch_hi}], N = E/2, sizes s^-2.5 on [2,25], Zipf(1.0)"
+            "config": {"workload": f"{G} hypergraphs, E log-uniform in [{lo}, "
+                                   f"{hi}], N = E/2, sizes s^-2.5 on [2,25], Zipf(1.0)"
                                    f" members, {R} randomized copies each (scaled-down variant of"
                                    f" E in [50000, 500000])",
                        "hypergraphs_counted": int(info["n_units"]),
@@ -557,12 +559,13 @@ def run_gpu(args):
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = _cpu_baseline(off, nodes, spec.n_nodes, args.cpu_seconds)
-    batch = serving = onthefly = None
+    batch = batch_small = serving = onthefly = None
     if ws == 1 and not args.no_extras:
         ctx.close()                       # free the medium line graph first
         if args.onthefly_r > 0:
             onthefly = _onthefly_measure(args)
         batch = _batch_measure(args)
+        batch_small = _batch_measure(args, 200, 2000)
         serving = _serving_measure(args)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -575,7 +578,8 @@ def run_gpu(args):
                                        f"independent hypergraph per rank x{ws}")},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk.summary(), "phases_ms": avg, "trace": st, "sampled": sampled,
-            "onthefly": onthefly, "batch": batch, "serving": serving}
+            "onthefly": onthefly, "batch": batch, "batch_small": batch_small,
+            "serving": serving}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
