@@ -61,6 +61,12 @@ UNIT = "triples/s"
 
 WORKLOADS = ("medium", "tiny", "zipf10k", "zipf40k")
 
+# DRAM bytes (read + write) of one k_dense_triangles launch, measured with
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass) on the
+# workload and threshold named, for the kernel as it is now (4-warp CTAs, 5
+# per SM); reported as null for any other workload or threshold.
+DENSE_TRAFFIC = {("medium", 1024): 9.962e12}
+
 
 def _spec(workload: str, seed_offset: int):
     """The bench workload (medium) or a smaller case of the same shape for
@@ -547,7 +553,9 @@ def run_gpu(args):
         n_t = float(st.get("heavy_bitmaps", 0)) / hw
         loads = words * 4.0 * (3 + 3 + 4 + n_t)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": args.traffic_bytes,
+                "frac": achieved / peak,
+                "traffic": (args.traffic_bytes if args.traffic_bytes is not None else
+                            DENSE_TRAFFIC.get((args.workload, int(st.get("dense_threshold", 0))))),
                 "kernel": "k_dense_triangles", "kernel_ms": avg[dom], "peak_kind": peak_kind,
                 "candidates_per_launch": cand, "bytes_per_candidate": 5,
                 "l2_term": {"bytes_per_candidate": 15, "achieved_gbs": 15.0 * cand / sec / 1e9},
