@@ -22,10 +22,12 @@
 //      e_j| are bit-sliced (3 bits and an overflow flag) from the bitmaps and
 //      lists of the nodes of each part; omega_ik = xa + xt, omega_jk = xb +
 //      xt and the triple intersection xt give the seven regions (Lemma
-//      "motif:time").  Candidates are grouped per warp by (xa, xb, xt,
-//      effective size) in a shared table and classified once per group at
-//      the end of the hyperwedge; larger counts are classified from node
-//      lists.
+//      "motif:time").  For theta = 1 the four commonest (xa, xb, xt) are
+//      popcounted per size class; other candidates are grouped per warp by
+//      (xa, xb, xt, effective size) in a shared table and classified once
+//      per group at the end of the hyperwedge, counts of 4 to 7 are
+//      classified at once, and only counts of 8 or more (the slices'
+//      overflow) from node lists.
 // Every classified instance equals the projected MoCHy-A+'s for the same
 // draws, so raw counts and estimates are the same bit for bit.
 #include "classify.cuh"
@@ -98,10 +100,22 @@ struct OtfWarp {
   int64_t lpos[kOtfNodes], lend[kOtfNodes];
   int64_t lnext[kOtfNodes];       // id of the list's next entry (INT64_MAX when done)
   uint32_t lw[32];                // one list's entries of a chunk, as word masks
+  int64_t lmin;                   // smallest next entry over the lists
   int32_t nh, nl;
   uint32_t table[kOtfKeys];
   uint32_t dirty[kOtfKeys / 32];
 };
+
+// smallest next entry over the warp's lists, into me.lmin (warp-wide)
+__device__ __forceinline__ void update_lmin(OtfWarp& me) {
+  const int lane = threadIdx.x & 31;
+  int64_t best = INT64_MAX;
+  for (int q = lane; q < me.nl; q += 32) best = min(best, me.lnext[q]);
+  for (int d = 16; d; d >>= 1) best = min(best, (int64_t)__shfl_xor_sync(0xffffffffu, best, d));
+  __syncwarp();
+  if (lane == 0) me.lmin = best;
+  __syncwarp();
+}
 
 // Sort the nodes of e (a = 0) or of e_i and e_j (a = 2) into bitmap and list
 // nodes with their parts; list cursors start at the first entry >= from.
@@ -157,6 +171,7 @@ __device__ void split_nodes(const OtfArgs& g, OtfWarp& me, int A, int B, bool pa
       __syncwarp();
     }
   }
+  update_lmin(me);
 }
 
 // The bit-sliced counters of the 32 words [w0, w0 + 32) of the three parts
@@ -184,6 +199,7 @@ __device__ __forceinline__ void gather_chunk(const OtfArgs& g, OtfWarp& me, int6
   // list nodes: a list's entries are distinct hyperedges, so its entries in
   // this chunk are one mask per word (shared-memory OR), added once per list
   const int64_t hi = (w0 + 32) * 32;
+  if (me.lmin >= hi) return;           // uniform: no list has an entry here
   for (int q = 0; q < nl; ++q) {
     if (me.lnext[q] >= hi) continue;   // uniform: nothing of this list here
     const int p = me.lpart[q];
@@ -215,17 +231,13 @@ __device__ __forceinline__ void gather_chunk(const OtfArgs& g, OtfWarp& me, int6
     else if (p == 1) slice_add(s.c[1][0], s.c[1][1], s.c[1][2], s.c[1][3], m);
     else slice_add(s.c[2][0], s.c[2][1], s.c[2][2], s.c[2][3], m);
   }
+  update_lmin(me);
 }
 
 // first word, at or after w0, that holds an entry of a list node (for
 // scans without bitmap nodes); W when none is left
 __device__ __forceinline__ int64_t next_list_word(const OtfArgs& g, const OtfWarp& me) {
-  const int lane = threadIdx.x & 31;
-  int64_t best = g.W;
-  for (int q = lane; q < me.nl; q += 32)
-    if (me.lnext[q] != INT64_MAX) best = min(best, me.lnext[q] >> 5);
-  for (int d = 16; d; d >>= 1) best = min(best, (int64_t)__shfl_xor_sync(0xffffffffu, best, d));
-  return best;
+  return me.lmin == INT64_MAX ? g.W : min(g.W, me.lmin >> 5);
 }
 
 __device__ __forceinline__ uint32_t any_of(const Slices& s, int p) {
@@ -482,8 +494,12 @@ __global__ void __launch_bounds__(kOtfThreads) k_otf_sample(OtfArgs g) {
           const int xb = sval(sc[1][0], sc[1][1], sc[1][2], bit);
           const int xt = sval(sc[2][0], sc[2][1], sc[2][2], bit);
           const int ce = min(C, xa + xb + 2 * xt + theta + 1);
-          if (!((so >> bit) & 1u) && xa < 4 && xb < 4 && xt < 4 && ce <= kOtfCeff) {
+          const bool over = (so >> bit) & 1u;   // some count is 8 or more
+          if (!over && xa < 4 && xb < 4 && xt < 4 && ce <= kOtfCeff) {
             key = ((xa * 4 + xb) * 4 + xt) * kOtfCeff + ce - 1;
+          } else if (!over) {
+            // counts below 8 are exact: classified at once
+            atomicAdd(&hist[lut[ternary_code(A, B, C, x, xb + xt, xa + xt, xt, theta)]], 1ull);
           } else {
             int z, y, t;
             exact_overlaps(me.anodes, A, me.bnodes, B, g.enode + g.eoff[k], C, z, y, t);
