@@ -299,13 +299,14 @@ def _onthefly_measure(args):
     time with CUDA events on the library's stream."""
     import torch
     from paper_2310_15668_gb300 import binding as B, synth
+    spec = synth.LARGE if args.onthefly_workload == "large" else _spec(args.onthefly_workload, 0)
     t = time.perf_counter()
-    off, nodes = synth.generate(synth.LARGE)
+    off, nodes = synth.generate(spec)
     gen_s = time.perf_counter() - t
     r = int(args.onthefly_r)
     with B.Context() as c:
         stream = torch.cuda.ExternalStream(c.stream)
-        c.load(synth.LARGE.n_nodes, off, nodes)
+        c.load(spec.n_nodes, off, nodes)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
@@ -331,8 +332,8 @@ def _onthefly_measure(args):
             "value": cands / (ms / 1000.0), "unit": "candidates/s", "r": r,
             "candidates_per_call": cands, "ms_per_call": ms, "calls": args.sampled_steps,
             "setup_ms": setup_ms, "hyperwedges": int(first[4]),
-            "config": {"workload": f"large: {synth.LARGE.describe()}, r = {r} hyperwedges by "
-                                   f"Philox seed 2 (+ call index)",
+            "config": {"workload": f"{args.onthefly_workload}: {spec.describe()}, r = {r} "
+                                   f"hyperwedges by Philox seed 2 (+ call index)",
                        "line_graph_bytes_if_projected": int(first[4]) * 16},
             "generate_s": gen_s,
             "trace": {k: tr.get(k) for k in ("otf_candidates", "otf_words", "otf_list_entries",
@@ -611,6 +612,9 @@ def main():
                     help="with several ranks: count one hypergraph with its rows shared out")
     ap.add_argument("--onthefly-r", type=int, default=2_000_000,
                     help="MoCHy-A+ draws on the large workload without a line graph (0: skip)")
+    ap.add_argument("--onthefly-workload", choices=["large"] + list(WORKLOADS), default="large")
+    ap.add_argument("--only-onthefly", action="store_true",
+                    help="run only the MoCHy-A+ measurement without a line graph (a profiler case)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-seconds", type=float, default=10.0)
@@ -629,6 +633,13 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_onthefly:
+        import torch
+        torch.cuda.set_device(0)
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(_onthefly_measure(args)), flush=True)
+        return 0
     return run_gpu(args)
 
 

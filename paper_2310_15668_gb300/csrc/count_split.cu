@@ -420,7 +420,31 @@ __device__ __forceinline__ void flush_slot(WS& me, int q, unsigned long long* hi
   __syncwarp();
 }
 
-template <bool kTheta1, bool kSeg>
+// Candidates of word w (bits of e) whose overlap with e_a or e_b is 7 or
+// more, or whose triple intersection is 8 or more: classified from node
+// lists (e_b's read here).  Kept out of line: rare, and the word loop stays
+// small.  Called by the whole warp.
+__device__ __noinline__ void exact_candidates(const SplitArgs& g, uint32_t e, int64_t w,
+                                              const int32_t* anodes, int A, int32_t* bnodes,
+                                              int64_t b, int B, int x, unsigned long long* hist,
+                                              const uint16_t* lut, int theta) {
+  const int lane = threadIdx.x & 31;
+  if (lane < B) bnodes[lane] = g.enode[g.eoff[b] + lane];
+  if (lane + 32 < B) bnodes[lane + 32] = g.enode[g.eoff[b] + lane + 32];
+  __syncwarp();
+  while (__any_sync(0xffffffffu, e != 0u)) {
+    if (!e) continue;
+    const int bit = __ffs(e) - 1;
+    e &= e - 1;
+    const int64_t k = g.dense_row[w * 32 + bit];
+    const int64_t kb = g.eoff[k];
+    const int C = (int)(g.eoff[k + 1] - kb);
+    const Overlap o = overlaps(anodes, A, bnodes, B, g.enode + kb, C);
+    add_triangle(hist, lut, theta, A, B, C, x, o.y, o.z, o.t, 1);
+  }
+}
+
+template <bool kTheta1, bool kSeg, bool kStats>
 __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* hist = (unsigned long long*)smem;
@@ -478,7 +502,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
     const int64_t rb = g.noff[a], re = g.noff[a + 1];
     const int A = (int)(g.eoff[a + 1] - g.eoff[a]);
     if (threadIdx.x < A) anodes[threadIdx.x] = g.enode[g.eoff[a] + threadIdx.x];
-    if (g.stats && threadIdx.x == 0) atomicAdd(&g.stats[82], 1ull);
+    if (kStats && threadIdx.x == 0) atomicAdd(&g.stats[82], 1ull);
     // omega planes of row a (bits 0, 1, 2 of min(omega, 7)), indexed by word - WLO
     const uint32_t* AR = g.dbits + dboff + (int64_t)(ad - dbase) * 3 * WN;
     if (threadIdx.x == 0) row_next = rb;
@@ -492,19 +516,25 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
       const int64_t b = ent_id(eab);
       const int bd = g.dense_idx[b];
       if (bd <= ad) continue;                       // b must be dense and after a
-      const long long t_setup0 = g.stats ? clock64() : 0;
+      const long long t_setup0 = kStats ? clock64() : 0;
       const int B = ent_size(eab);
       const int x = entry_omega(eab.y, A);
-      if (lane < B) me.bnodes[lane] = g.enode[g.eoff[b] + lane];
-      if (lane + 32 < B) me.bnodes[lane + 32] = g.enode[g.eoff[b] + lane + 32];
+      if (A > kMaskedMax) {
+        // a wide row's entries hold omega, not node masks: e_b's nodes are
+        // needed for the membership tests below
+        if (lane < B) me.bnodes[lane] = g.enode[g.eoff[b] + lane];
+        if (lane + 32 < B) me.bnodes[lane + 32] = g.enode[g.eoff[b] + lane + 32];
+      }
       if (lane < 2) me.n[lane] = 0;
       __syncwarp();
       // the nodes of e_a & e_b (group T): with a bitmap ("heavy") or a short
-      // list of dense hyperedges ("light")
+      // list of dense hyperedges ("light"); for |e_a| <= 32 the entry (a, b)
+      // marks them (bit p: the p-th node of e_a lies in e_b)
       for (int base = 0; base < A; base += 32) {
         const int l = base + lane;
         const int32_t u = l < A ? anodes[l] : -1;
-        const bool inT = l < A && has_node(me.bnodes, B, u);
+        const bool inT = l < A && (A <= kMaskedMax ? ((eab.y >> l) & 1u) != 0u
+                                                   : has_node(me.bnodes, B, u));
         const int hv = inT ? g.heavy_idx[u] : -1;
         const bool hvy = inT && hv >= 0, lt = inT && hv < 0;
         const unsigned bh = __ballot_sync(0xffffffffu, hvy);
@@ -528,7 +558,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
       unsigned long long st_cand = 0, st_table = 0, st_exact = 0;
       const int64_t first = (int64_t)(bd + 1);
       const int64_t fw = first >> 5;
-      const long long t_groups = g.stats ? clock64() : 0;
+      const long long t_groups = kStats ? clock64() : 0;
       // light T nodes: their dense lists (fewer than 32 entries each) from
       // `first` on, merged into one ascending list when they fit, else read
       // through one cursor per node
@@ -551,7 +581,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
         n_lent += __popc(kb);
       }
       const bool merged = n_lent <= kLight;
-      const long long t_light = g.stats ? clock64() : 0;
+      const long long t_light = kStats ? clock64() : 0;
       if (merged && n_lent > 1) {
         // bitonic sort of the merged entries (padded to a power of two)
         int np = 2;
@@ -573,7 +603,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
       }
       __syncwarp();
       int lcur = 0;   // next merged entry
-      long long t_words0 = g.stats ? clock64() : 0;
+      long long t_words0 = kStats ? clock64() : 0;
       // uniform loop: every lane runs every iteration (lanes past the end see
       // an empty word), so the warp stays converged
       // the overlap planes of the 32 candidates of word w (omega_ak, omega_bk)
@@ -689,7 +719,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
             cnt[5 + c] += __popc(s110 & sc);
           }
         }
-        if (g.stats) {
+        if (kStats) {
           st_cand += __popc(m);
           st_table += __popc(valid & ~done);
           st_exact += __popc(ovf);
@@ -751,24 +781,15 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
             if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0) {
               atomicAdd(&me.table[key], (uint32_t)__popc(peers));
               atomicOr(&me.dirty[key >> 5], 1u << (key & 31));
-              if (g.stats) atomicAdd(&g.stats[8 + key / kCeff], (unsigned long long)__popc(peers));
+              if (kStats) atomicAdd(&g.stats[8 + key / kCeff], (unsigned long long)__popc(peers));
             }
           }
         }
-        uint32_t e = ovf;
-        while (__any_sync(0xffffffffu, e != 0u)) {
-          if (!e) continue;
-          const int bit = __ffs(e) - 1;
-          e &= e - 1;
-          const int64_t k = g.dense_row[w * 32 + bit];
-          const int64_t kb = g.eoff[k];
-          const int C = (int)(g.eoff[k + 1] - kb);
-          const Overlap o = overlaps(anodes, A, me.bnodes, B, g.enode + kb, C);
-          add_triangle(hist, lut, theta, A, B, C, x, o.y, o.z, o.t, 1);
-        }
+        if (__any_sync(0xffffffffu, ovf != 0u))
+          exact_candidates(g, ovf, w, anodes, A, me.bnodes, b, B, x, hist, lut, theta);
       }
-      long long t_words1 = g.stats ? clock64() : 0;
-      if (g.stats) {
+      long long t_words1 = kStats ? clock64() : 0;
+      if (kStats) {
         for (int d = 16; d; d >>= 1) {
           st_cand += __shfl_xor_sync(0xffffffffu, st_cand, d);
           st_table += __shfl_xor_sync(0xffffffffu, st_table, d);
@@ -808,7 +829,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
             q = me.snext;
             __syncwarp();
             if (lane == 0) me.snext = (q + 1) % kSlots;
-            if (g.stats && lane == 0) atomicAdd(&g.stats[80], 1ull);
+            if (kStats && lane == 0) atomicAdd(&g.stats[80], 1ull);
             flush_slot(me, q, hist, lut, A);
           }
           if (lane == 0) {
@@ -823,7 +844,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
         if (lane == 0) me.sn[q] = nq;
         __syncwarp();
         if (nq >= kSlotFlush) {
-          if (g.stats && lane == 0) atomicAdd(&g.stats[81], 1ull);
+          if (kStats && lane == 0) atomicAdd(&g.stats[81], 1ull);
           flush_slot(me, q, hist, lut, A);
         }
       } else {
@@ -852,7 +873,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
           add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, (long long)n);
         }
       }
-      if (g.stats && lane == 0) {
+      if (kStats && lane == 0) {
         const long long t_end = clock64();
         atomicAdd(&g.stats[5], (unsigned long long)(t_words0 - t_setup0));
         atomicAdd(&g.stats[72], (unsigned long long)(t_groups - t_setup0));
@@ -1556,6 +1577,14 @@ struct SplitPlan {
   int max_deg = 1;
 };
 
+// the dense-triangle kernel for theta = 1 or another theta, with or without
+// the tracing counters
+template <bool kSeg>
+static void (*dense_kernel(bool theta1, bool stats))(SplitArgs) {
+  if (theta1) return stats ? k_dense_triangles<true, kSeg, true> : k_dense_triangles<true, kSeg, false>;
+  return stats ? k_dense_triangles<false, kSeg, true> : k_dense_triangles<false, kSeg, false>;
+}
+
 template <bool kSeg>
 static int plan_kernels(mochy_ctx* ctx, SplitPlan* p) {
   if (ctx->n_sparse > 0) {
@@ -1572,7 +1601,7 @@ static int plan_kernels(mochy_ctx* ctx, SplitPlan* p) {
   }
   if (ctx->n_dense > 0) {
     const size_t smem = dense_smem_bytes(ctx->wmax);
-    auto kern = ctx->theta == 1 ? k_dense_triangles<true, kSeg> : k_dense_triangles<false, kSeg>;
+    auto kern = dense_kernel<kSeg>(ctx->theta == 1, p->g.stats != nullptr);
     MOCHY_TRY(ensure_dynamic_smem((const void*)kern, smem));
     int per_sm = 0;
     MOCHY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDThreads, smem));
@@ -1668,7 +1697,7 @@ static int launch_split(mochy_ctx* ctx, SplitPlan p, PhaseTimer* timer, const Wo
     g.order = wl.dense;
     g.n_order = wl.n_dense;
     g.queue = ctx->counters + 6;
-    auto kern = ctx->theta == 1 ? k_dense_triangles<true, kSeg> : k_dense_triangles<false, kSeg>;
+    auto kern = dense_kernel<kSeg>(ctx->theta == 1, g.stats != nullptr);
     kern<<<p.grid_dense, kDThreads, p.smem_dense, st>>>(g);
     MOCHY_LAUNCHED();
     if (timer) timer->mark("dense triangles");
