@@ -189,12 +189,19 @@ __device__ __forceinline__ void gather_chunk(const OtfArgs& g, OtfWarp& me, int6
   const int64_t w = w0 + lane;
   const bool inr = w < g.W;
   const int nh = me.nh, nl = me.nl;
-  for (int q = 0; q < nh; ++q) {
-    const uint32_t word = inr ? __ldg(&g.hbits[(int64_t)me.hb[q] * g.W + w]) : 0u;
-    const int p = me.hpart[q];
-    if (p == 0) slice_add(s.c[0][0], s.c[0][1], s.c[0][2], s.c[0][3], word);
-    else if (p == 1) slice_add(s.c[1][0], s.c[1][1], s.c[1][2], s.c[1][3], word);
-    else slice_add(s.c[2][0], s.c[2][1], s.c[2][2], s.c[2][3], word);
+  // bitmap nodes, eight loads in flight before their words are added
+  for (int q0 = 0; q0 < nh; q0 += 8) {
+    uint32_t wd[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      wd[u] = (inr && q0 + u < nh) ? __ldg(&g.hbits[(int64_t)me.hb[q0 + u] * g.W + w]) : 0u;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int p = q0 + u < nh ? me.hpart[q0 + u] : 3;   // 3: no node (word 0)
+      if (p == 0) slice_add(s.c[0][0], s.c[0][1], s.c[0][2], s.c[0][3], wd[u]);
+      else if (p == 1) slice_add(s.c[1][0], s.c[1][1], s.c[1][2], s.c[1][3], wd[u]);
+      else if (p == 2) slice_add(s.c[2][0], s.c[2][1], s.c[2][2], s.c[2][3], wd[u]);
+    }
   }
   // list nodes: a list's entries are distinct hyperedges, so its entries in
   // this chunk are one mask per word (shared-memory OR), added once per list
