@@ -362,7 +362,9 @@ int mochy_profile_batch(const mochy_config* cfg, int32_t n_graphs, const int64_t
  * batching: n_slots worker threads, each with a context and a CUDA stream of
  * its own, take queued requests in arrival order as soon as a slot is free
  * and the request's estimated device memory fits the budget beside the
- * requests already running (cfg->hbm_budget_bytes, else 70% of the device
+ * requests already running (a later request that fits may start before an
+ * earlier one that does not, but at most 32 times for any one request:
+ * then later requests wait until it fits) (cfg->hbm_budget_bytes, else 70% of the device
  * memory free at creation), so requests that arrive while others run start
  * as slots and memory free up and their work overlaps on the device.  A
  * request runs exactly the calls a direct caller would make (mochy_load,

@@ -32,6 +32,9 @@ void release_scratch(mochy_ctx* ctx);                 // api.cu
 
 namespace {
 
+// a queued request is overtaken by at most this many later ones
+constexpr int32_t kMaxBypass = 32;
+
 struct Request {
   int64_t ticket = 0;
   int32_t kind = 0;
@@ -43,6 +46,7 @@ struct Request {
   int32_t n_random = 0;
   uint64_t seed = 0;
   int64_t est = 0;
+  int32_t bypassed = 0;      // later requests admitted while this one waited
   bool onthefly = false;     // MoCHy-A+ without the line graph
   int64_t otf_budget = 0;    // its bitmap budget, bytes
   double t_submit = 0.0;
@@ -151,14 +155,19 @@ void worker_main(mochy_server* s) {
       std::unique_lock<std::mutex> lk(s->mu);
       auto fits = [&]() -> std::deque<std::unique_ptr<Request>>::iterator {
         // first request in arrival order that fits beside the running ones
-        // (a request alone always fits: larger ones are refused at submit)
-        for (auto it = s->pending.begin(); it != s->pending.end(); ++it)
+        // (a request alone always fits: larger ones are refused at submit);
+        // once the oldest one has been overtaken kMaxBypass times, nothing
+        // overtakes it any more: the others wait until it fits
+        for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
           if (s->in_flight == 0 || s->reserved + (*it)->est <= s->budget) return it;
+          if (it == s->pending.begin() && (*it)->bypassed >= kMaxBypass) break;
+        }
         return s->pending.end();
       };
       s->cv_work.wait(lk, [&] { return s->stop || fits() != s->pending.end(); });
       if (s->stop) break;
       auto it = fits();
+      if (it != s->pending.begin()) s->pending.front()->bypassed += 1;
       r = std::move(*it);
       s->pending.erase(it);
       s->reserved += r->est;

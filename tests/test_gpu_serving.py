@@ -148,3 +148,27 @@ def test_large_aplus_requests_run_without_the_line_graph():
     with B.Context() as c:
         c.load(*g)
         assert r["n_wedges"] == c.project()[0]
+
+
+def test_large_request_is_not_overtaken_forever():
+    """A request too large to start beside the running ones may be overtaken
+    by later, smaller requests, but only a bounded number of times: with 60
+    small requests queued behind it, it starts before the last of them, and
+    every result is still the one the same call gives alone."""
+    big, small = _zipf(3000, 81), _zipf(800, 82)
+    est_big, est_small = _estimate(*big), _estimate(*small)
+    assert est_big > 3 * est_small
+    budget = est_big + est_small + est_small // 2     # the big one needs all but one small
+    with B.Server(n_slots=4, budget=budget) as srv:
+        first = [srv.submit(B.MOCHY_REQ_EXACT, *small) for _ in range(3)]
+        t_big = srv.submit(B.MOCHY_REQ_EXACT, *big)
+        rest = [srv.submit(B.MOCHY_REQ_EXACT, *small) for _ in range(60)]
+        res = {t: srv.poll(t, wait_ms=300000) for t in first + [t_big] + rest}
+    assert all(r is not None and r["status"] >= 0 for r in res.values())
+    start = {t: r["latency_ms"] - r["service_ms"] for t, r in res.items()}
+    # some small request queued behind the big one started after it
+    assert max(start[t] for t in rest) > start[t_big]
+    _check_same(res[t_big], _alone(B.MOCHY_REQ_EXACT, big))
+    ref_small = _alone(B.MOCHY_REQ_EXACT, small)
+    for t in first + rest:
+        _check_same(res[t], ref_small)
