@@ -340,6 +340,45 @@ def _onthefly_measure(args):
                                              "otf_exact", "otf_bitmaps")}}
 
 
+def _extensions_measure(args):
+    """kh-motifs (k = 4, thresholds 1 and 2), instance enumeration and radial
+    node profiles, each one timed call through the C ABI (host results
+    included) on a seeded Zipf hypergraph of the medium shape, scaled down:
+    their per-instance scans suit hypergraphs of up to about 1e10 triples."""
+    from paper_2310_15668_gb300 import binding as B, synth
+    out = {}
+
+    def timed(fn):
+        fn()                                   # warm-up (tables, allocation)
+        t = time.perf_counter()
+        r = fn()
+        return r, time.perf_counter() - t
+
+    g4 = synth.HypergraphSpec(2000, 4000, 2, 25, "powerlaw", 2.5, "zipf", 1.0, seed=6)
+    off, nodes = synth.generate(g4)
+    with B.Context() as c:
+        c.load(g4.n_nodes, off, nodes)
+        c.project()
+        (h, kh), dt = timed(lambda: c.count_kh(4, (1, 2)))
+        out["kh4"] = {"metric": "instances classified/s into 3,076 4h-motifs", "value":
+                      float(h.sum()) / dt, "seconds": dt, "instances": int(h.sum()),
+                      "workload": g4.describe()}
+    g1 = synth.HypergraphSpec(500, 1000, 2, 25, "powerlaw", 2.5, "zipf", 1.0, seed=3)
+    off, nodes = synth.generate(g1)
+    with B.Context() as c:
+        c.load(g1.n_nodes, off, nodes)
+        c.project()
+        n_inst = int(c.count_exact()[0].sum())
+        (rows, n), dt = timed(lambda: c.enumerate(n_inst))
+        out["enumerate"] = {"metric": "instances written/s (i, j, k, h, 3h rows)", "value":
+                            n / dt, "seconds": dt, "instances": int(n),
+                            "workload": g1.describe()}
+        (rh, r3), dt = timed(lambda: c.radial_node_profile())
+        out["radial_np"] = {"metric": "radial node profiles/s", "value": g1.n_nodes / dt,
+                            "seconds": dt, "nodes": g1.n_nodes, "workload": g1.describe()}
+    return out
+
+
 def _batch_measure(args, lo=None, hi=None):
     """CPs/s of the batched profile against one profile call per hypergraph."""
     from paper_2310_15668_gb300 import binding as B, synth
@@ -568,7 +607,7 @@ def run_gpu(args):
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = _cpu_baseline(off, nodes, spec.n_nodes, args.cpu_seconds)
-    batch = batch_small = serving = onthefly = None
+    batch = batch_small = serving = onthefly = extensions = None
     if ws == 1 and not args.no_extras:
         ctx.close()                       # free the medium line graph first
         if args.onthefly_r > 0:
@@ -576,6 +615,7 @@ def run_gpu(args):
         batch = _batch_measure(args)
         batch_small = _batch_measure(args, 200, 2000)
         serving = _serving_measure(args)
+        extensions = _extensions_measure(args)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "int64",
@@ -588,7 +628,7 @@ def run_gpu(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk.summary(), "phases_ms": avg, "trace": st, "sampled": sampled,
             "onthefly": onthefly, "batch": batch, "batch_small": batch_small,
-            "serving": serving}
+            "serving": serving, "extensions": extensions}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0

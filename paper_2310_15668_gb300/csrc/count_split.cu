@@ -27,6 +27,7 @@
 // are enumerated from a staged copy of that member's row.
 #include <cstdio>
 #include <cstdlib>
+#include <type_traits>
 
 #include "classify.cuh"
 
@@ -610,6 +611,12 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
       // and their size planes are loaded one iteration ahead, so that a
       // warp has the next chunk's loads in flight while it works on this one
       // (and the bitmap word of the first heavy node of e_a & e_b, if any)
+      // The word loop, compiled twice: for the common hyperwedge whose
+      // e_a & e_b is one node with a bitmap (no other heavy node, no light
+      // node) and for any other; the first leaves out the bit-sliced sum over
+      // several T nodes and the merge of light lists, so its loop is shorter.
+      auto word_loop = [&](auto simple) {
+        constexpr bool kSimple = decltype(simple)::value;
       const uint32_t* T0 = NB + (nT > 0 ? (int64_t)me.hidx[0] * WN : 0);
       uint32_t nqa0 = 0, nqa1 = 0, nqa2 = 0, nqb0 = 0, nqb1 = 0, nqb2 = 0;
       uint32_t np0 = 0, np1 = 0, np2 = 0, np3 = 0, nt = 0;
@@ -639,8 +646,11 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
         if (w == fw) m &= 0xffffffffu << (first & 31);
         // xt = |e_a & e_b & e_k|, bit-sliced (3 bits and an overflow flag)
         uint32_t t0 = tb, t1 = 0, t2 = 0, ovf = 0;   // tb: the first heavy node's word
-        for (int h = 1; h < nT; ++h)
-          slice_add(t0, t1, t2, ovf, __ldg(&NB[(int64_t)me.hidx[h] * WN + wl]));
+        if constexpr (!kSimple) {
+          for (int h = 1; h < nT; ++h)
+            slice_add(t0, t1, t2, ovf, __ldg(&NB[(int64_t)me.hidx[h] * WN + wl]));
+        }
+        if constexpr (!kSimple) {
         // light T nodes with a dense index in this iteration's 32 words
         const int64_t hi64 = (w0 + 32) * 32;
         const int32_t hi = hi64 < 0x7fffffff ? (int32_t)hi64 : 0x7fffffff;
@@ -673,6 +683,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
             }
             __syncwarp();
           }
+        }
         }
         // omega >= 7 or xt >= 8: classified from node lists below
         ovf = (ovf | (qa0 & qa1 & qa2) | (qb0 & qb1 & qb2)) & m;
@@ -788,6 +799,9 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
         if (__any_sync(0xffffffffu, ovf != 0u))
           exact_candidates(g, ovf, w, anodes, A, me.bnodes, b, B, x, hist, lut, theta);
       }
+      };
+      if (nT == 1 && nL == 0) word_loop(std::true_type{});
+      else word_loop(std::false_type{});
       long long t_words1 = kStats ? clock64() : 0;
       if (kStats) {
         for (int d = 16; d; d >>= 1) {
