@@ -68,7 +68,7 @@ struct Tables {
 // One hypergraph ("unit") of a batch counted as a disjoint union: where its
 // dense rows and heavy nodes sit in the split structures.  Its dense rows are
 // the dense indices [dbase, dbase + n); their bitmaps cover only the unit's
-// window of words [wlo, wlo + wn) and start at word dboff of dbits (2 wn words
+// window of words [wlo, wlo + wn) and start at word dboff of dbits (4 wn words
 // a row); its heavy nodes are the heavy indices from hbase on, with bitmaps
 // of wn words from word nboff of nbits.  A lone hypergraph is one unit with
 // wlo = 0 and wn = the number of dense words.
@@ -126,10 +126,12 @@ struct mochy_ctx {
   int64_t n_dense = 0, n_sparse = 0, n_heavy = 0, wwords = 0;
   int32_t* dense_idx = nullptr;   // [E]  dense index or -1
   int32_t* dense_row = nullptr;   // [n_dense]
-  uint32_t* dbits = nullptr;      // per dense row 3 planes over its window: bits of min(omega, 7)
+  uint32_t* dbits = nullptr;      // per dense row, per word of its window, 4 words: bits 0..2
+                                  // of min(omega, 7) and the mask of omega >= 1
   int32_t* heavy_idx = nullptr;   // [N]  heavy index or -1
   uint32_t* nbits = nullptr;      // [n_heavy][wwords]  dense members of E_v
-  uint32_t* sbits = nullptr;      // [5][wwords]  size class of dense rows
+  uint32_t* sbits = nullptr;      // per word 4 words (bits 0..3 of min(|e_k|, 15)),
+                                  // then [5][wwords] size classes of dense rows
   int32_t* dense_order = nullptr;   // dense rows by decreasing work
   int32_t* sparse_order = nullptr;  // sparse rows by decreasing work
   int64_t* dvoff = nullptr;         // [N+1] dense members of E_v ...
@@ -159,7 +161,7 @@ struct mochy_ctx {
   size_t otf_bytes = 0;
   int32_t* otf_hidx = nullptr;     // [N] bitmap index or -1
   uint32_t* otf_hbits = nullptr;   // [otf_bitmaps][otf_words]
-  uint32_t* otf_sbits = nullptr;   // [4][otf_words]
+  uint32_t* otf_sbits = nullptr;   // per word 4 words: bits 0..3 of min(|e_k|, 15)
   int64_t* otf_uprefix = nullptr;  // [E+1]
   int64_t otf_wedges = 0, otf_bitmaps = 0, otf_words = 0;
 

@@ -276,8 +276,10 @@ __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
 // ---------------------------------------------------------------------------
 // Triangles with three dense rows: CTA per dense row a, warp per hyperwedge
 // (a, b).  Every dense row keeps its overlaps with the other dense rows of
-// its hypergraph as three bit-planes over the dense index (bits 0, 1, 2 of
-// min(omega, 7)), 32 candidates per word.  For a candidate e_k
+// its hypergraph as bit-planes over the dense index, interleaved so that a
+// word of the row is one 16-byte load: bits 0, 1, 2 of min(omega, 7) and the
+// mask of adjacent candidates, 32 candidates per word (the four size planes
+// are interleaved the same way).  For a candidate e_k
 // adjacent to both e_a and e_b, with xa, xb, xt the numbers of nodes of
 // e_a \ e_b, e_b \ e_a and e_a & e_b that e_k holds,
 //   omega_ak = xa + xt,  omega_bk = xb + xt,
@@ -470,10 +472,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
   if (lane == 0) me.snext = 0;
   __syncwarp();
   const int theta = g.theta;
-  const uint32_t* P0 = g.sbits;
-  const uint32_t* P1 = g.sbits + W;
-  const uint32_t* P2 = g.sbits + 2 * W;
-  const uint32_t* P3 = g.sbits + 3 * W;
+  const uint4* PS = (const uint4*)g.sbits;   // size planes, four words per word
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -505,7 +504,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
     if (threadIdx.x < A) anodes[threadIdx.x] = g.enode[g.eoff[a] + threadIdx.x];
     if (kStats && threadIdx.x == 0) atomicAdd(&g.stats[82], 1ull);
     // omega planes of row a (bits 0, 1, 2 of min(omega, 7)), indexed by word - WLO
-    const uint32_t* AR = g.dbits + dboff + (int64_t)(ad - dbase) * 3 * WN;
+    const uint4* AR = (const uint4*)(g.dbits + dboff + (int64_t)(ad - dbase) * 4 * WN);
     if (threadIdx.x == 0) row_next = rb;
     __syncthreads();
     while (true) {
@@ -551,7 +550,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
         __syncwarp();
       }
       const int nT = me.n[0], nL = me.n[1];
-      const uint32_t* BR = g.dbits + dboff + (int64_t)(bd - dbase) * 3 * WN;
+      const uint4* BR = (const uint4*)(g.dbits + dboff + (int64_t)(bd - dbase) * 4 * WN);
       // per-lane counters: 14 pairs of 16-bit bins (theta = 1) or 10 bins
       uint32_t cnt[14];
 #pragma unroll
@@ -618,31 +617,32 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
       auto word_loop = [&](auto simple) {
         constexpr bool kSimple = decltype(simple)::value;
       const uint32_t* T0 = NB + (nT > 0 ? (int64_t)me.hidx[0] * WN : 0);
-      uint32_t nqa0 = 0, nqa1 = 0, nqa2 = 0, nqb0 = 0, nqb1 = 0, nqb2 = 0;
-      uint32_t np0 = 0, np1 = 0, np2 = 0, np3 = 0, nt = 0;
+      uint4 nqa = make_uint4(0u, 0u, 0u, 0u), nqb = nqa, np = nqa;
+      uint32_t nt = 0;
       if (fw < WHI) {
         const int64_t w = fw + lane < WHI ? fw + lane : WHI - 1;
         const int64_t wl = w - WLO;
-        nqa0 = __ldg(&AR[wl]); nqa1 = __ldg(&AR[WN + wl]); nqa2 = __ldg(&AR[2 * WN + wl]);
-        nqb0 = __ldg(&BR[wl]); nqb1 = __ldg(&BR[WN + wl]); nqb2 = __ldg(&BR[2 * WN + wl]);
-        np0 = __ldg(&P0[w]); np1 = __ldg(&P1[w]); np2 = __ldg(&P2[w]); np3 = __ldg(&P3[w]);
+        nqa = __ldg(&AR[wl]);
+        nqb = __ldg(&BR[wl]);
+        np = __ldg(&PS[w]);
         if (nT > 0) nt = __ldg(&T0[wl]);
       }
       for (int64_t w0 = fw; w0 < WHI; w0 += 32) {
         const bool inr = w0 + lane < WHI;
         const int64_t w = inr ? w0 + lane : WHI - 1;
         const int64_t wl = w - WLO;
-        const uint32_t qa0 = nqa0, qa1 = nqa1, qa2 = nqa2, qb0 = nqb0, qb1 = nqb1, qb2 = nqb2;
-        const uint32_t p0 = np0, p1 = np1, p2 = np2, p3 = np3, tb = nt;
+        const uint32_t qa0 = nqa.x, qa1 = nqa.y, qa2 = nqa.z, qb0 = nqb.x, qb1 = nqb.y, qb2 = nqb.z;
+        const uint32_t anya = nqa.w, anyb = nqb.w;
+        const uint32_t p0 = np.x, p1 = np.y, p2 = np.z, p3 = np.w, tb = nt;
         {
           const int64_t w1 = w0 + 32 + lane < WHI ? w0 + 32 + lane : WHI - 1;
           const int64_t wl1 = w1 - WLO;
-          nqa0 = __ldg(&AR[wl1]); nqa1 = __ldg(&AR[WN + wl1]); nqa2 = __ldg(&AR[2 * WN + wl1]);
-          nqb0 = __ldg(&BR[wl1]); nqb1 = __ldg(&BR[WN + wl1]); nqb2 = __ldg(&BR[2 * WN + wl1]);
-          np0 = __ldg(&P0[w1]); np1 = __ldg(&P1[w1]); np2 = __ldg(&P2[w1]); np3 = __ldg(&P3[w1]);
+          nqa = __ldg(&AR[wl1]);
+          nqb = __ldg(&BR[wl1]);
+          np = __ldg(&PS[w1]);
           if (nT > 0) nt = __ldg(&T0[wl1]);
         }
-        uint32_t m = inr ? ((qa0 | qa1 | qa2) & (qb0 | qb1 | qb2)) : 0u;
+        uint32_t m = inr ? (anya & anyb) : 0u;
         if (w == fw) m &= 0xffffffffu << (first & 31);
         // xt = |e_a & e_b & e_k|, bit-sliced (3 bits and an overflow flag)
         uint32_t t0 = tb, t1 = 0, t2 = 0, ovf = 0;   // tb: the first heavy node's word
@@ -982,14 +982,14 @@ __global__ void __launch_bounds__(kThreads) k_sparse_triangles(SplitArgs g, int 
       if (bd >= 0) {
         // b dense: every k after b is dense with a larger dense index
         // omega planes of row b: omega_bk = bit0 + 2 bit1 + 4 bit2 (7: 7 or more)
-        const uint32_t* Q = g.dbits + dboff + (int64_t)(bd - dbase) * 3 * WN;
+        const uint4* Q = (const uint4*)(g.dbits + dboff + (int64_t)(bd - dbase) * 4 * WN);
         for (int q = lane; q < deg; q += 32) {
           const int kd = sdi[q];
           if (kd <= bd) continue;
           const uint32_t bit = 1u << (kd & 31);
           const int64_t wq = (kd >> 5) - WLO;
-          const uint32_t q0 = __ldg(&Q[wq]) & bit, q1 = __ldg(&Q[WN + wq]) & bit,
-                         q2 = __ldg(&Q[2 * WN + wq]) & bit;
+          const uint4 qw = __ldg(&Q[wq]);
+          const uint32_t q0 = qw.x & bit, q1 = qw.y & bit, q2 = qw.z & bit;
           if (!(q0 | q1 | q2)) continue;
           const int64_t k = skey[q];
           const int C = ssz[q];
@@ -1111,17 +1111,20 @@ __global__ void k_dense_bits(int64_t n_dense, const SegInfo* __restrict__ seg,
     const SegInfo sg = seg[seg_of(dbase, n_units, r)];
     const int64_t b = drow[r];
     const int B = (int)(eoff[b + 1] - eoff[b]);
-    uint32_t* Q = dbits + sg.dboff + (r - sg.dbase) * 3 * sg.wn;
+    // word wq of the row is four words: bits 0, 1, 2 of min(omega, 7) and
+    // the mask of adjacent candidates (omega >= 1)
+    uint32_t* Q = dbits + sg.dboff + (r - sg.dbase) * 4 * sg.wn;
     for (int64_t p = noff[b] + threadIdx.x; p < noff[b + 1]; p += blockDim.x) {
       const uint2 e = nadj[p];
       const int kd = didx[ent_id(e)];
       if (kd < 0) continue;
       const int om = min(entry_omega(e.y, B), 7);   // 7 stands for 7 or more
-      const int64_t wq = (kd >> 5) - sg.wlo;
+      const int64_t wq = 4 * ((kd >> 5) - sg.wlo);
       const uint32_t bit = 1u << (kd & 31);
       if (om & 1) atomicOr(&Q[wq], bit);
-      if (om & 2) atomicOr(&Q[sg.wn + wq], bit);
-      if (om & 4) atomicOr(&Q[2 * sg.wn + wq], bit);
+      if (om & 2) atomicOr(&Q[wq + 1], bit);
+      if (om & 4) atomicOr(&Q[wq + 2], bit);
+      atomicOr(&Q[wq + 3], bit);
     }
   }
 }
@@ -1223,8 +1226,8 @@ __global__ void k_size_bits(int64_t n_dense, int64_t W, const int32_t* __restric
   const int C = (int)(eoff[k + 1] - eoff[k]);
   dsize[r] = (uint8_t)C;
   const int cc = min(C, 15);
-  for (int b = 0; b < 4; ++b)
-    if (cc & (1 << b)) atomicOr(&sbits[(int64_t)b * W + (r >> 5)], 1u << (r & 31));
+  for (int b = 0; b < 4; ++b)   // word w of the size planes is four words: bits 0..3
+    if (cc & (1 << b)) atomicOr(&sbits[4 * (int64_t)(r >> 5) + b], 1u << (r & 31));
   const int c = size_class(C, theta);
   atomicOr(&sbits[(int64_t)(4 + c) * W + (r >> 5)], 1u << (r & 31));
 }
@@ -1375,7 +1378,7 @@ int prepare_split(mochy_ctx* ctx) {
     sg.wlo = hdb[u] >> 5;
     sg.wn = nd > 0 ? ((hdb[u + 1] + 31) >> 5) - sg.wlo : 0;
     sg.dboff = dwords;
-    dwords += nd * 3 * sg.wn;
+    dwords += nd * 4 * sg.wn;
     sg.hbase = sg.nboff = 0;
     wmax = std::max(wmax, sg.wn);
   }

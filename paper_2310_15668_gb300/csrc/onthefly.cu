@@ -51,7 +51,7 @@ struct OtfArgs {
   const int32_t* vedge;
   const int32_t* hidx;            // [N] bitmap index of a node, or -1
   const uint32_t* hbits;          // [n_bitmaps][W]
-  const uint32_t* sbits;          // [4][W] bits 0..3 of min(|e_k|, 15)
+  const uint32_t* sbits;          // per word 4 words: bits 0..3 of min(|e_k|, 15)
   const int64_t* uprefix;         // [E+1] exclusive prefix of the neighbours after i
   int64_t n_wedges;
   const uint16_t* lut3;
@@ -429,9 +429,8 @@ __global__ void __launch_bounds__(kOtfThreads) k_otf_sample(OtfArgs g) {
       if (w == (j >> 5)) m &= ~(1u << (j & 31));
       st_words += inr ? 1 : 0;
       st_cand += __popc(m);
-      const uint32_t p0 = inr ? __ldg(&g.sbits[w]) : 0u, p1 = inr ? __ldg(&g.sbits[g.W + w]) : 0u;
-      const uint32_t p2 = inr ? __ldg(&g.sbits[2 * g.W + w]) : 0u;
-      const uint32_t p3 = inr ? __ldg(&g.sbits[3 * g.W + w]) : 0u;
+      const uint4 ps = inr ? __ldg(&((const uint4*)g.sbits)[w]) : make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t p0 = ps.x, p1 = ps.y, p2 = ps.z, p3 = ps.w;
       const uint32_t ovf = s.c[0][3] | s.c[1][3] | s.c[2][3];
       if (theta == 1) {
         const uint32_t az = ~(s.c[0][0] | s.c[0][1] | s.c[0][2] | s.c[0][3]);
@@ -593,7 +592,7 @@ __global__ void k_otf_size_bits(int64_t E, int64_t W, const uint8_t* __restrict_
   if (k >= E) return;
   const int c = min((int)esize[k], 15);
   for (int b = 0; b < 4; ++b)
-    if (c & (1 << b)) atomicOr(&sbits[(int64_t)b * W + (k >> 5)], 1u << (k & 31));
+    if (c & (1 << b)) atomicOr(&sbits[4 * (k >> 5) + b], 1u << (k & 31));
 }
 
 }  // namespace
