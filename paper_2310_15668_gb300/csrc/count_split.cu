@@ -739,8 +739,8 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
         // lane i takes the i-th remaining candidate of the iteration (from any
         // lane's word), reads that word's planes by shuffle, and equal
         // (combination, size) keys are added once per group of lanes
-        {
-          const uint32_t rest = valid & ~done;
+        const uint32_t rest = valid & ~done;
+        if (__any_sync(0xffffffffu, rest != 0u)) {
           const int rc = __popc(rest);
           int incl = rc;
 #pragma unroll
