@@ -617,33 +617,35 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
       auto word_loop = [&](auto simple) {
         constexpr bool kSimple = decltype(simple)::value;
       const uint32_t* T0 = NB + (nT > 0 ? (int64_t)me.hidx[0] * WN : 0);
+      // word indices fit in 32 bits (at most 2^21 words)
+      const int iWHI = (int)WHI, iWLO = (int)WLO, ifw = (int)fw;
       uint4 nqa = make_uint4(0u, 0u, 0u, 0u), nqb = nqa, np = nqa;
       uint32_t nt = 0;
-      if (fw < WHI) {
-        const int64_t w = fw + lane < WHI ? fw + lane : WHI - 1;
-        const int64_t wl = w - WLO;
+      if (ifw < iWHI) {
+        const int w = ifw + lane < iWHI ? ifw + lane : iWHI - 1;
+        const int wl = w - iWLO;
         nqa = __ldg(&AR[wl]);
         nqb = __ldg(&BR[wl]);
         np = __ldg(&PS[w]);
         if (nT > 0) nt = __ldg(&T0[wl]);
       }
-      for (int64_t w0 = fw; w0 < WHI; w0 += 32) {
-        const bool inr = w0 + lane < WHI;
-        const int64_t w = inr ? w0 + lane : WHI - 1;
-        const int64_t wl = w - WLO;
+      for (int w0 = ifw; w0 < iWHI; w0 += 32) {
+        const bool inr = w0 + lane < iWHI;
+        const int w = inr ? w0 + lane : iWHI - 1;
+        const int wl = w - iWLO;
         const uint32_t qa0 = nqa.x, qa1 = nqa.y, qa2 = nqa.z, qb0 = nqb.x, qb1 = nqb.y, qb2 = nqb.z;
         const uint32_t anya = nqa.w, anyb = nqb.w;
         const uint32_t p0 = np.x, p1 = np.y, p2 = np.z, p3 = np.w, tb = nt;
         {
-          const int64_t w1 = w0 + 32 + lane < WHI ? w0 + 32 + lane : WHI - 1;
-          const int64_t wl1 = w1 - WLO;
+          const int w1 = w0 + 32 + lane < iWHI ? w0 + 32 + lane : iWHI - 1;
+          const int wl1 = w1 - iWLO;
           nqa = __ldg(&AR[wl1]);
           nqb = __ldg(&BR[wl1]);
           np = __ldg(&PS[w1]);
           if (nT > 0) nt = __ldg(&T0[wl1]);
         }
         uint32_t m = inr ? (anya & anyb) : 0u;
-        if (w == fw) m &= 0xffffffffu << (first & 31);
+        if (w == ifw) m &= 0xffffffffu << (first & 31);
         // xt = |e_a & e_b & e_k|, bit-sliced (3 bits and an overflow flag)
         uint32_t t0 = tb, t1 = 0, t2 = 0, ovf = 0;   // tb: the first heavy node's word
         if constexpr (!kSimple) {
@@ -652,7 +654,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
         }
         if constexpr (!kSimple) {
         // light T nodes with a dense index in this iteration's 32 words
-        const int64_t hi64 = (w0 + 32) * 32;
+        const int64_t hi64 = (int64_t)(w0 + 32) * 32;
         const int32_t hi = hi64 < 0x7fffffff ? (int32_t)hi64 : 0x7fffffff;
         if (merged) {
           while (lcur < n_lent) {
@@ -660,7 +662,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
             const int nin = __popc(__ballot_sync(0xffffffffu, e < hi && e != 0x7fffffff));
             for (int j = 0; j < nin; ++j) {
               const int32_t kd = __shfl_sync(0xffffffffu, e, j);
-              if ((int64_t)(kd >> 5) == w && inr) slice_add(t0, t1, t2, ovf, 1u << (kd & 31));
+              if ((kd >> 5) == w && inr) slice_add(t0, t1, t2, ovf, 1u << (kd & 31));
             }
             lcur += nin;
             if (nin < 32) break;
@@ -673,7 +675,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
             const int nin = __popc(__ballot_sync(0xffffffffu, e < hi));
             for (int j = 0; j < nin; ++j) {
               const int32_t kd = __shfl_sync(0xffffffffu, e, j);
-              if ((int64_t)(kd >> 5) == w && inr) slice_add(t0, t1, t2, ovf, 1u << (kd & 31));
+              if ((kd >> 5) == w && inr) slice_add(t0, t1, t2, ovf, 1u << (kd & 31));
             }
             const int32_t nx = __shfl_sync(0xffffffffu, e, nin & 31);
             __syncwarp();
@@ -769,7 +771,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
                            st2 = __shfl_sync(0xffffffffu, t2, src);
             const uint32_t sp0 = __shfl_sync(0xffffffffu, p0, src), sp1 = __shfl_sync(0xffffffffu, p1, src),
                            sp2 = __shfl_sync(0xffffffffu, p2, src), sp3 = __shfl_sync(0xffffffffu, p3, src);
-            const int64_t sw = __shfl_sync(0xffffffffu, w, src);
+            const int sw = __shfl_sync(0xffffffffu, w, src);
             const bool act = item < total;
             int key = -1;
             int xa = 0, xb = 0, xt = 0, ce = 0;
@@ -780,7 +782,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
               xb = sval3(sb0, sb1, sb2, bit) - xt;
               int C = (int)((sp0 >> bit) & 1u) | ((int)((sp1 >> bit) & 1u) << 1) |
                       ((int)((sp2 >> bit) & 1u) << 2) | ((int)((sp3 >> bit) & 1u) << 3);
-              if (C >= 15) C = g.dsize[sw * 32 + bit];
+              if (C >= 15) C = g.dsize[(int64_t)sw * 32 + bit];
               ce = min(C, xa + xb + 2 * xt + theta + 1);
               if (xa < 4 && xb < 4 && xt < 4 && ce <= kCeff)
                 key = ((xa * 4 + xb) * 4 + xt) * kCeff + ce - 1;
