@@ -298,8 +298,11 @@ __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
 // per SM (80 registers, spilling; 27.3 s): 22.8 s
 constexpr int kDThreads = 128;
 constexpr int kDWarps = kDThreads / 32;
-constexpr int kCeff = 16;          // effective sizes kept in the table
 constexpr int kCombo = 64;         // (xa, xb, xt) with each count below 4
+// effective sizes per combination kept in the table, as the offset
+// ce - (xa + xb + xt) (the effective size lies in [xa + xb + xt,
+// xa + xb + 2 xt + theta + 1]: 6 values for theta = 1)
+constexpr int kRel = 8;
 
 constexpr int kLight = 256;        // merged light-node entries per hyperwedge (a power of two)
 constexpr int kSlots = 8;          // per-warp signature slots of popcounted bins (theta = 1)
@@ -314,8 +317,7 @@ struct WarpScratch {
   int32_t hidx[64];      // heavy indices of the nodes of e_a & e_b
   int32_t light[64];     // the nodes of e_a & e_b without a bitmap
   int32_t n[2];          // how many of each
-  uint32_t table[kCombo * kCeff];
-  uint32_t dirty[kCombo * kCeff / 32];
+  uint32_t table[kCombo * kRel];
   // theta = 1: totals of the popcounted bins summed over the row's
   // hyperwedges that share a signature (their motif codes are equal)
   uint32_t sacc[kSlots][32];
@@ -462,8 +464,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
   WarpScratch& me = ws[warp];
   int cur = 0;   // unit whose counts the shared histogram holds (kSeg)
   load_lut(lut, g.lut3, hist);
-  for (int q = lane; q < kCombo * kCeff; q += 32) me.table[q] = 0u;
-  me.dirty[lane] = 0u;
+  for (int q = lane; q < kCombo * kRel; q += 32) me.table[q] = 0u;
   for (int q = 0; q < kSlots; ++q) me.sacc[q][lane] = 0u;
   if (lane < kSlots) {
     me.skey[lane] = -1;
@@ -614,6 +615,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
       // e_a & e_b is one node with a bitmap (no other heavy node, no light
       // node) and for any other; the first leaves out the bit-sliced sum over
       // several T nodes and the merge of light lists, so its loop is shorter.
+      uint32_t dmask = 0u;   // groups of 32 table entries this lane touched
       auto word_loop = [&](auto simple) {
         constexpr bool kSimple = decltype(simple)::value;
       const uint32_t* T0 = NB + (nT > 0 ? (int64_t)me.hidx[0] * WN : 0);
@@ -737,66 +739,31 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
           st_table += __popc(valid & ~done);
           st_exact += __popc(ovf);
         }
-        // remaining candidates, processed by the whole warp 32 at a time:
-        // lane i takes the i-th remaining candidate of the iteration (from any
-        // lane's word), reads that word's planes by shuffle, and equal
-        // (combination, size) keys are added once per group of lanes
-        const uint32_t rest = valid & ~done;
-        if (__any_sync(0xffffffffu, rest != 0u)) {
-          const int rc = __popc(rest);
-          int incl = rc;
-#pragma unroll
-          for (int d = 1; d < 32; d <<= 1) {
-            const int o = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += o;
-          }
-          const int total = __shfl_sync(0xffffffffu, incl, 31);
-          for (int base = 0; base < total; base += 32) {
-            const int item = base + lane;
-            // source lane: the first lane whose inclusive count exceeds item
-            int src = 0;
-#pragma unroll
-            for (int st = 16; st; st >>= 1) {
-              const int probe = __shfl_sync(0xffffffffu, incl, src + st - 1);
-              if (probe <= item) src += st;
-            }
-            src &= 31;
-            const int ex = __shfl_sync(0xffffffffu, incl - rc, src);
-            const uint32_t rs = __shfl_sync(0xffffffffu, rest, src);
-            const uint32_t sa0 = __shfl_sync(0xffffffffu, qa0, src), sa1 = __shfl_sync(0xffffffffu, qa1, src),
-                           sa2 = __shfl_sync(0xffffffffu, qa2, src);
-            const uint32_t sb0 = __shfl_sync(0xffffffffu, qb0, src), sb1 = __shfl_sync(0xffffffffu, qb1, src),
-                           sb2 = __shfl_sync(0xffffffffu, qb2, src);
-            const uint32_t st0 = __shfl_sync(0xffffffffu, t0, src), st1 = __shfl_sync(0xffffffffu, t1, src),
-                           st2 = __shfl_sync(0xffffffffu, t2, src);
-            const uint32_t sp0 = __shfl_sync(0xffffffffu, p0, src), sp1 = __shfl_sync(0xffffffffu, p1, src),
-                           sp2 = __shfl_sync(0xffffffffu, p2, src), sp3 = __shfl_sync(0xffffffffu, p3, src);
-            const int sw = __shfl_sync(0xffffffffu, w, src);
-            const bool act = item < total;
-            int key = -1;
-            int xa = 0, xb = 0, xt = 0, ce = 0;
-            if (act) {
-              const int bit = __fns(rs, 0, item - ex + 1);
-              xt = sval3(st0, st1, st2, bit);
-              xa = sval3(sa0, sa1, sa2, bit) - xt;
-              xb = sval3(sb0, sb1, sb2, bit) - xt;
-              int C = (int)((sp0 >> bit) & 1u) | ((int)((sp1 >> bit) & 1u) << 1) |
-                      ((int)((sp2 >> bit) & 1u) << 2) | ((int)((sp3 >> bit) & 1u) << 3);
-              if (C >= 15) C = g.dsize[(int64_t)sw * 32 + bit];
-              ce = min(C, xa + xb + 2 * xt + theta + 1);
-              if (xa < 4 && xb < 4 && xt < 4 && ce <= kCeff)
-                key = ((xa * 4 + xb) * 4 + xt) * kCeff + ce - 1;
-            }
-            if (act && key < 0) {
+        // remaining candidates: each lane classifies those of its own word,
+        // one at a time, into the table (or straight into the histogram when
+        // the combination or the offset is outside it)
+        uint32_t rest = valid & ~done;
+        if (rest) {
+          do {
+            const int bit = __ffs(rest) - 1;
+            rest &= rest - 1u;
+            const int xt = sval3(t0, t1, t2, bit);
+            const int xa = sval3(qa0, qa1, qa2, bit) - xt;
+            const int xb = sval3(qb0, qb1, qb2, bit) - xt;
+            int C = (int)((p0 >> bit) & 1u) | ((int)((p1 >> bit) & 1u) << 1) |
+                    ((int)((p2 >> bit) & 1u) << 2) | ((int)((p3 >> bit) & 1u) << 3);
+            if (C >= 15) C = g.dsize[(int64_t)w * 32 + bit];
+            const int ce = min(C, xa + xb + 2 * xt + theta + 1);
+            const int rel = ce - (xa + xb + xt);
+            if (xa < 4 && xb < 4 && xt < 4 && rel >= 0 && rel < kRel) {
+              const int key = ((xa * 4 + xb) * 4 + xt) * kRel + rel;
+              atomicAdd(&me.table[key], 1u);
+              dmask |= 1u << (key >> 5);
+              if (kStats) atomicAdd(&g.stats[8 + key / kRel], 1ull);
+            } else {
               add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, 1);
             }
-            const unsigned peers = __match_any_sync(0xffffffffu, key);
-            if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0) {
-              atomicAdd(&me.table[key], (uint32_t)__popc(peers));
-              atomicOr(&me.dirty[key >> 5], 1u << (key & 31));
-              if (kStats) atomicAdd(&g.stats[8 + key / kCeff], (unsigned long long)__popc(peers));
-            }
-          }
+          } while (rest);
         }
         if (__any_sync(0xffffffffu, ovf != 0u))
           exact_candidates(g, ovf, w, anodes, A, me.bnodes, b, B, x, hist, lut, theta);
@@ -875,18 +842,16 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
         }
       }
       __syncwarp();
-      {
-        uint32_t dw = me.dirty[lane];
-        me.dirty[lane] = 0u;
-        while (dw) {
-          const int q = lane * 32 + __ffs(dw) - 1;
-          dw &= dw - 1;
-          const uint32_t n = me.table[q];
+      // the table entries of this hyperwedge, one group of 32 at a time
+      for (uint32_t gm = __reduce_or_sync(0xffffffffu, dmask); gm; gm &= gm - 1u) {
+        const int q = (__ffs(gm) - 1) * 32 + lane;
+        const uint32_t n = me.table[q];
+        if (n) {
           me.table[q] = 0u;
-          if (!n) continue;
-          const int ce = q % kCeff + 1, combo = q / kCeff;
+          const int combo = q / kRel, rel = q % kRel;
           const int xt = combo & 3, xb = (combo >> 2) & 3, xa = combo >> 4;
-          add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, (long long)n);
+          add_triangle(hist, lut, theta, A, B, xa + xb + xt + rel, x, xb + xt, xa + xt, xt,
+                       (long long)n);
         }
       }
       if (kStats && lane == 0) {
