@@ -60,8 +60,16 @@ __device__ inline int class_rep(int c, int theta) {
   return c == 0 ? 1 : c == 1 ? 2 : c == 2 ? 3 : c == 3 ? theta + 2 : theta + 3;
 }
 
+// h[id] += v on a 64-bit bin in shared memory, as a 32-bit atomic add on its
+// low word plus, when that add carries out or v is negative, an add of the
+// carry and v's high word to the high word (bins are only read once every
+// add has completed)
 __device__ __forceinline__ void hadd(unsigned long long* h, int id, long long v) {
-  atomicAdd(&h[id], (unsigned long long)v);
+  unsigned int* w = reinterpret_cast<unsigned int*>(h + id);
+  const unsigned int u = (unsigned int)v;
+  const unsigned int old = atomicAdd(w, u);
+  const unsigned int adj = (old + u < old ? 1u : 0u) + (unsigned int)((unsigned long long)v >> 32);
+  if (adj) atomicAdd(w + 1, adj);
 }
 
 // One closed instance {a, b, k} with sizes A, B, C, omega_ab = x,
@@ -74,6 +82,27 @@ __device__ __forceinline__ void add_triangle(unsigned long long* hist, const uin
   if (x + z <= A) hadd(hist, lut[ternary_code(A, B, C, x, 0, z, 0, theta)], -n);
   if (x + y <= B) hadd(hist, lut[ternary_code(B, A, C, x, 0, y, 0, theta)], -n);
   if (z + y <= C) hadd(hist, lut[ternary_code(C, A, B, z, 0, y, 0, theta)], -n);
+}
+
+// n closed instances of one table key of hyperwedge (a, b): A = |e_a|,
+// B = |e_b|, omega_ab = x, and a third hyperedge holding xa nodes of
+// e_a \ e_b, xb of e_b \ e_a and xt of both, with effective size
+// xa + xb + xt + rel.  The same codes as add_triangle with y = xb + xt,
+// z = xa + xt, t = xt, written with the regions that involve the third
+// hyperedge already reduced.
+__device__ __forceinline__ void add_key(unsigned long long* hist, const uint16_t* lut, int theta,
+                                        int A, int B, int x, int xa, int xb, int xt, int rel,
+                                        long long n) {
+  auto st = [theta](int r) { return (r > 0 ? 1 : 0) + (r > theta ? 1 : 0); };
+  const int y = xb + xt, z = xa + xt;
+  hadd(hist, lut[st(A - x - xa) + 3 * st(B - x - xb) + 9 * st(rel) + 27 * st(x - xt) +
+                 81 * st(xb) + 243 * st(xa) + 729 * st(xt)], n);
+  if (x + z <= A)
+    hadd(hist, lut[st(A - x - z) + 3 * st(B - x) + 9 * st(xb + rel) + 27 * st(x) + 243 * st(z)], -n);
+  if (x + y <= B)
+    hadd(hist, lut[st(B - x - y) + 3 * st(A - x) + 9 * st(xa + rel) + 27 * st(x) + 243 * st(y)], -n);
+  if (xt <= rel)
+    hadd(hist, lut[st(rel - xt) + 3 * st(A - z) + 9 * st(B - y) + 27 * st(z) + 243 * st(y)], -n);
 }
 
 // binary search of node u in an ascending list in shared memory
@@ -850,8 +879,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
           me.table[q] = 0u;
           const int combo = q / kRel, rel = q % kRel;
           const int xt = combo & 3, xb = (combo >> 2) & 3, xa = combo >> 4;
-          add_triangle(hist, lut, theta, A, B, xa + xb + xt + rel, x, xb + xt, xa + xt, xt,
-                       (long long)n);
+          add_key(hist, lut, theta, A, B, x, xa, xb, xt, rel, (long long)n);
         }
       }
       if (kStats && lane == 0) {
