@@ -63,9 +63,10 @@ WORKLOADS = ("medium", "tiny", "zipf10k", "zipf40k")
 
 # DRAM bytes (read + write) of one k_dense_triangles launch, measured with
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass) on the
-# workload and threshold named, for the kernel as it is now (4-warp CTAs, 5
-# per SM); reported as null for any other workload or threshold.
-DENSE_TRAFFIC = {("medium", 1024): 9.962e12}
+# workload and threshold named, for the kernel as it is now; reported as
+# null for any other workload or threshold, and emptied whenever the kernel
+# changes until it is measured again.
+DENSE_TRAFFIC = {}
 
 
 def _spec(workload: str, seed_offset: int):
