@@ -768,31 +768,81 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dense_triangles(SplitArgs g) {
           st_table += __popc(valid & ~done);
           st_exact += __popc(ovf);
         }
-        // remaining candidates: each lane classifies those of its own word,
-        // one at a time, into the table (or straight into the histogram when
-        // the combination or the offset is outside it)
+        // remaining candidates, classified into the table (or straight into
+        // the histogram when the combination or the offset is outside it)
+        auto classify_rest = [&](uint32_t ra0, uint32_t ra1, uint32_t ra2, uint32_t rb0,
+                                 uint32_t rb1, uint32_t rb2, uint32_t rt0, uint32_t rt1,
+                                 uint32_t rt2, uint32_t rp0, uint32_t rp1, uint32_t rp2,
+                                 uint32_t rp3, int rw, int bit) {
+          const int xt = sval3(rt0, rt1, rt2, bit);
+          const int xa = sval3(ra0, ra1, ra2, bit) - xt;
+          const int xb = sval3(rb0, rb1, rb2, bit) - xt;
+          int C = (int)((rp0 >> bit) & 1u) | ((int)((rp1 >> bit) & 1u) << 1) |
+                  ((int)((rp2 >> bit) & 1u) << 2) | ((int)((rp3 >> bit) & 1u) << 3);
+          if (C >= 15) C = g.dsize[(int64_t)rw * 32 + bit];
+          const int ce = min(C, xa + xb + 2 * xt + theta + 1);
+          const int rel = ce - (xa + xb + xt);
+          if (xa < 4 && xb < 4 && xt < 4 && rel >= 0 && rel < kRel) {
+            const int key = ((xa * 4 + xb) * 4 + xt) * kRel + rel;
+            atomicAdd(&me.table[key], 1u);
+            dmask |= 1u << (key >> 5);
+            if (kStats) atomicAdd(&g.stats[8 + key / kRel], 1ull);
+          } else {
+            add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, 1);
+          }
+        };
         uint32_t rest = valid & ~done;
-        if (rest) {
-          do {
-            const int bit = __ffs(rest) - 1;
-            rest &= rest - 1u;
-            const int xt = sval3(t0, t1, t2, bit);
-            const int xa = sval3(qa0, qa1, qa2, bit) - xt;
-            const int xb = sval3(qb0, qb1, qb2, bit) - xt;
-            int C = (int)((p0 >> bit) & 1u) | ((int)((p1 >> bit) & 1u) << 1) |
-                    ((int)((p2 >> bit) & 1u) << 2) | ((int)((p3 >> bit) & 1u) << 3);
-            if (C >= 15) C = g.dsize[(int64_t)w * 32 + bit];
-            const int ce = min(C, xa + xb + 2 * xt + theta + 1);
-            const int rel = ce - (xa + xb + xt);
-            if (xa < 4 && xb < 4 && xt < 4 && rel >= 0 && rel < kRel) {
-              const int key = ((xa * 4 + xb) * 4 + xt) * kRel + rel;
-              atomicAdd(&me.table[key], 1u);
-              dmask |= 1u << (key >> 5);
-              if (kStats) atomicAdd(&g.stats[8 + key / kRel], 1ull);
-            } else {
-              add_triangle(hist, lut, theta, A, B, ce, x, xb + xt, xa + xt, xt, 1);
+        if constexpr (!kSeg) {
+          // one hypergraph: each lane takes the remaining candidates of its
+          // own word, one at a time
+          if (rest) {
+            do {
+              const int bit = __ffs(rest) - 1;
+              rest &= rest - 1u;
+              classify_rest(qa0, qa1, qa2, qb0, qb1, qb2, t0, t1, t2, p0, p1, p2, p3, w, bit);
+            } while (rest);
+          }
+        } else {
+          // a batch of hypergraphs: spread over the warp, 32 per round (lane l
+          // takes the l-th remaining candidate of the iteration and reads its
+          // word's planes by shuffle)
+          if (__any_sync(0xffffffffu, rest != 0u)) {
+            const int rc = __popc(rest);
+            int incl = rc;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+              const int o = __shfl_up_sync(0xffffffffu, incl, d);
+              if (lane >= d) incl += o;
             }
-          } while (rest);
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int base = 0; base < total; base += 32) {
+              const int item = base + lane;
+              // source lane: the first lane whose inclusive count exceeds item
+              int src = 0;
+#pragma unroll
+              for (int st = 16; st; st >>= 1) {
+                const int probe = __shfl_sync(0xffffffffu, incl, src + st - 1);
+                if (probe <= item) src += st;
+              }
+              src &= 31;
+              const int ex = __shfl_sync(0xffffffffu, incl - rc, src);
+              uint32_t rs = __shfl_sync(0xffffffffu, rest, src);
+              const uint32_t sa0 = __shfl_sync(0xffffffffu, qa0, src), sa1 = __shfl_sync(0xffffffffu, qa1, src),
+                             sa2 = __shfl_sync(0xffffffffu, qa2, src);
+              const uint32_t sb0 = __shfl_sync(0xffffffffu, qb0, src), sb1 = __shfl_sync(0xffffffffu, qb1, src),
+                             sb2 = __shfl_sync(0xffffffffu, qb2, src);
+              const uint32_t st0 = __shfl_sync(0xffffffffu, t0, src), st1 = __shfl_sync(0xffffffffu, t1, src),
+                             st2 = __shfl_sync(0xffffffffu, t2, src);
+              const uint32_t sp0 = __shfl_sync(0xffffffffu, p0, src), sp1 = __shfl_sync(0xffffffffu, p1, src),
+                             sp2 = __shfl_sync(0xffffffffu, p2, src), sp3 = __shfl_sync(0xffffffffu, p3, src);
+              const int sw = __shfl_sync(0xffffffffu, w, src);
+              if (item < total) {
+                for (int k = item - ex; k > 0; --k) rs &= rs - 1u;   // its (item - ex)-th bit
+                classify_rest(sa0, sa1, sa2, sb0, sb1, sb2, st0, st1, st2, sp0, sp1, sp2, sp3, sw,
+                              __ffs(rs) - 1);
+              }
+            }
+          }
         }
         if (__any_sync(0xffffffffu, ovf != 0u))
           exact_candidates(g, ovf, w, anodes, A, me.bnodes, b, B, x, hist, lut, theta);
