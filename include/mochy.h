@@ -70,6 +70,13 @@ typedef struct {
                                per-hyperwedge scan; both give the same counts */
   int32_t dense_threshold;  /* split kernel: line degree from which a row is
                                kept as a bitmap; 0 = chosen by the tuner */
+  int32_t rest_path;        /* split kernel, closed candidates of dense rows
+                               outside the popcounted combinations: 1 = each
+                               lane classifies those of its own word, 2 = they
+                               are spread over the warp 32 at a time, 0 = 1 when
+                               the dense rows span at least 2,048 words of 32
+                               rows, else 2 (a batch always spreads them); all
+                               give the same counts */
 } mochy_config;
 
 /* Fill *cfg with the defaults above. */

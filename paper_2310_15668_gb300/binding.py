@@ -48,7 +48,7 @@ class mochy_config(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_int32), ("eps", ctypes.c_double),
                 ("hbm_budget_bytes", ctypes.c_int64), ("device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("exact_kernel", ctypes.c_int32),
-                ("dense_threshold", ctypes.c_int32)]
+                ("dense_threshold", ctypes.c_int32), ("rest_path", ctypes.c_int32)]
 
 
 class mochy_batch_info(ctypes.Structure):
@@ -455,7 +455,7 @@ class Context:
 
     def __init__(self, theta: int = 1, eps: float = 1.0, budget: int = 0, device: int = 0,
                  stream: int | None = None, handle: int | None = None, exact_kernel: int = 0,
-                 dense_threshold: int = 0):
+                 dense_threshold: int = 0, rest_path: int = 0):
         if handle is not None:
             self.h = handle
         else:
@@ -463,6 +463,7 @@ class Context:
             cfg.theta, cfg.eps, cfg.hbm_budget_bytes, cfg.device = theta, eps, budget, device
             cfg.stream = stream
             cfg.exact_kernel, cfg.dense_threshold = exact_kernel, dense_threshold
+            cfg.rest_path = rest_path
             self.h = mochy_create(cfg)
 
     def close(self):

@@ -196,6 +196,7 @@ void mochy_config_default(mochy_config* cfg) {
   cfg->stream = nullptr;
   cfg->exact_kernel = 0;
   cfg->dense_threshold = 0;
+  cfg->rest_path = 0;
 }
 
 int mochy_create(mochy_ctx** out, const mochy_config* cfg_in) {
@@ -208,6 +209,7 @@ int mochy_create(mochy_ctx** out, const mochy_config* cfg_in) {
   if (!(cfg.eps >= 0.0)) return fail(MOCHY_E_INVALID, "eps must be >= 0");
   if (cfg.exact_kernel < 0 || cfg.exact_kernel > 1) return fail(MOCHY_E_INVALID, "bad exact_kernel");
   if (cfg.dense_threshold < 0) return fail(MOCHY_E_INVALID, "bad dense_threshold");
+  if (cfg.rest_path < 0 || cfg.rest_path > 2) return fail(MOCHY_E_INVALID, "bad rest_path");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -222,6 +224,7 @@ int mochy_create(mochy_ctx** out, const mochy_config* cfg_in) {
   ctx->budget = cfg.hbm_budget_bytes;
   ctx->exact_kernel = cfg.exact_kernel;
   ctx->dense_thr = cfg.dense_threshold;
+  ctx->rest_path = cfg.rest_path;
   memset(ctx->last_stats, 0, sizeof(ctx->last_stats));
   int rc = MOCHY_OK;
   auto bail = [&](int code) {
@@ -716,6 +719,7 @@ static int new_like(mochy_ctx* src, mochy_ctx** out) {
   cfg.stream = src->own_stream ? nullptr : (void*)src->stream;
   cfg.exact_kernel = src->exact_kernel;
   cfg.dense_threshold = src->dense_thr;
+  cfg.rest_path = src->rest_path;
   return mochy_create(out, &cfg);
 }
 

@@ -121,6 +121,7 @@ struct mochy_ctx {
   // dense-row index space; nodes with >= heavy_thr dense hyperedges get one too.
   int exact_kernel = 0;          // 0 split (default), 1 wedge-scan
   int32_t dense_thr = 0;         // 0 = chosen by the tuner
+  int32_t rest_path = 0;         // dense candidates outside the bins: 0 auto, 1 per lane, 2 spread
   int32_t heavy_thr = 32;
   bool split_ready = false;
   int64_t n_dense = 0, n_sparse = 0, n_heavy = 0, wwords = 0;

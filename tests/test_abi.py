@@ -47,3 +47,20 @@ def test_strerror_without_gpu(lib):
     lib.mochy_strerror.restype = ctypes.c_char_p
     assert lib.mochy_strerror(0) == b"ok"
     assert b"device memory" in lib.mochy_strerror(-2)
+
+
+def test_config_defaults_and_validation_without_gpu():
+    """mochy_config_default fills every field of the header's struct (the
+    binding's layout matches it), and mochy_create refuses a bad rest_path
+    before it looks for a device."""
+    from paper_2310_15668_gb300 import binding as B
+    cfg = B.mochy_config()
+    ctypes.memset(ctypes.byref(cfg), 0x5A, ctypes.sizeof(cfg))
+    B.load_library().mochy_config_default(ctypes.byref(cfg))
+    assert (cfg.theta, cfg.eps, cfg.hbm_budget_bytes, cfg.device) == (1, 1.0, 0, 0)
+    assert (cfg.exact_kernel, cfg.dense_threshold, cfg.rest_path) == (0, 0, 0)
+    for bad in (-1, 3):
+        cfg.rest_path = bad
+        with pytest.raises(B.MochyError) as e:
+            B.mochy_create(cfg)
+        assert e.value.code == -1 and "rest_path" in str(e.value)

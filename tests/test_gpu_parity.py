@@ -77,7 +77,11 @@ def test_load_and_project(ctx, name):
 # exact-count kernels: the per-hyperwedge scan, and the split kernel with the
 # tuned threshold, with (nearly) every row dense, and with a middle threshold
 VARIANTS = {"scan": dict(exact_kernel=1), "split": dict(), "dense": dict(dense_threshold=2),
-            "mixed": dict(dense_threshold=24)}
+            "mixed": dict(dense_threshold=24),
+            # the same with the dense rows' remaining candidates taken per lane
+            # (small hypergraphs spread them over the warp by default)
+            "dense_lane": dict(dense_threshold=2, rest_path=1),
+            "mixed_lane": dict(dense_threshold=24, rest_path=1)}
 
 
 @pytest.fixture(scope="module")
@@ -122,7 +126,7 @@ def test_split_matches_scan_on_larger_zipf_graph(variant_ctx):
 
 
 @pytest.mark.parametrize("theta", [2, 3])
-@pytest.mark.parametrize("variant", ["scan", "split", "dense"])
+@pytest.mark.parametrize("variant", ["scan", "split", "dense", "dense_lane"])
 @pytest.mark.parametrize("name", ["wide", "zipf_small"])
 def test_exact_counts_other_theta(theta, variant, name):
     n, off, nodes = GRAPHS[name]

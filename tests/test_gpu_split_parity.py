@@ -91,11 +91,14 @@ def _split_rank(deg, thr):
     return np.where(deg < thr, ids, (1 + deg.astype(np.int64)) * e + ids)
 
 
+@pytest.mark.parametrize("rest_path", [1, 2])
 @pytest.mark.parametrize("name", sorted(GRAPHS))
-def test_split_kernel_matches_oracle_on_multichunk_graphs(name):
+def test_split_kernel_matches_oracle_on_multichunk_graphs(name, rest_path):
+    """rest_path 1: each lane classifies the remaining candidates of its own
+    word (the path of large hypergraphs); 2: they are spread over the warp."""
     n, off, nodes = _graph(name)
     thr = GRAPHS[name][1]
-    with B.Context(dense_threshold=thr) as c:
+    with B.Context(dense_threshold=thr, rest_path=rest_path) as c:
         c.load(n, off, nodes)
         c.project()
         B.mochy_trace(c.h, 2)
@@ -115,10 +118,11 @@ def test_split_kernel_matches_oracle_on_multichunk_graphs(name):
         assert tr["exact_candidates"] > 0
 
 
-def test_split_kernel_other_theta_on_multichunk_graph():
+@pytest.mark.parametrize("rest_path", [1, 2])
+def test_split_kernel_other_theta_on_multichunk_graph(rest_path):
     """theta = 2: the size-class bins of the kernel's other variant."""
     n, off, nodes = _graph("zipf6k_clusters")
-    with B.Context(theta=2, dense_threshold=32) as c:
+    with B.Context(theta=2, dense_threshold=32, rest_path=rest_path) as c:
         c.load(n, off, nodes)
         c.project()
         h, h3 = c.count_exact()
