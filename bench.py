@@ -421,6 +421,20 @@ def _batch_measure(args, lo=None, hi=None):
                                                "ms_count", "ms_finish")}}
 
 
+def _tuner_measure(ctx, st):
+    """The measured dense-threshold tuner on the bench hypergraph, after the
+    timed steps: each of its candidate thresholds times the dense count of
+    the same 2 % row sample with CUDA events, and the fastest is its pick;
+    reported beside the threshold the timed steps used."""
+    from paper_2310_15668_gb300 import binding as B
+    t = time.perf_counter()
+    best, tried = B.mochy_tune_dense_threshold(ctx.h)
+    return {"kind": "measured (CUDA events on a 2 % row sample per candidate)",
+            "threshold_of_timed_steps": int(st.get("dense_threshold", 0)), "best": int(best),
+            "candidates_ms": {str(int(thr)): float(ms) for thr, ms in tried},
+            "seconds": time.perf_counter() - t}
+
+
 def _serving_measure(args):
     """Latency and throughput of a Poisson request stream on a mochy_server."""
     import threading
@@ -605,6 +619,9 @@ def run_gpu(args):
     sampled = None
     if args.sampled_r > 0:
         sampled = _sampled_measure(ctx, args)
+    tuner = None
+    if ws == 1 and not shard and not args.no_tuner:
+        tuner = _tuner_measure(ctx, st)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = _cpu_baseline(off, nodes, spec.n_nodes, args.cpu_seconds)
@@ -628,6 +645,7 @@ def run_gpu(args):
                                        f"independent hypergraph per rank x{ws}")},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk.summary(), "phases_ms": avg, "trace": st, "sampled": sampled,
+            "tuner": tuner,
             "onthefly": onthefly, "batch": batch, "batch_small": batch_small,
             "serving": serving, "extensions": extensions}
     print(json.dumps(line), flush=True)
@@ -660,6 +678,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tuner", action="store_true",
+                    help="skip the measured threshold tuner after the timed steps")
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving lines")
     ap.add_argument("--batch-graphs", type=int, default=16)
     ap.add_argument("--batch-copies", type=int, default=32)
