@@ -316,15 +316,19 @@ __global__ void __launch_bounds__(kOpenThreads) k_open_pairs(SplitArgs g) {
 // (3 bits and an overflow flag) from the bitmaps of the nodes of e_a & e_b
 // ("heavy" nodes) or their short lists of dense hyperedges ("light" ones).
 // The usual combinations (xa, xb, xt) are counted by popcount per size bin;
-// any other goes to a per-warp table keyed by (xa, xb, xt, effective size);
-// a candidate with an omega of 7 or more, or xt >= 8, is classified from
-// node lists.
+// any other goes to a per-warp table keyed by (xa, xb, xt, effective size),
+// each such candidate classified by the lane whose word holds it (large
+// windows, where they are rare) or spread over the warp 32 at a time; a
+// candidate with an omega of 7 or more, or xt >= 8, is classified from node
+// lists.
 // Shared layout: hist | lut | anodes[64] | WarpScratch[kDWarps]
 // ---------------------------------------------------------------------------
-// 4 warps per CTA and 5 CTAs per SM (96 registers, 42 KB of shared memory
-// per CTA): 20 resident warps per SM; measured on the medium workload
-// against 8-warp CTAs at 2 per SM (16 warps, 125 registers; 24.0 s) and at 3
-// per SM (80 registers, spilling; 27.3 s): 22.8 s
+// 4 warps per CTA and 5 CTAs per SM (96 registers, 32 KB of shared memory
+// per CTA): 20 resident warps per SM.  Measured on the medium workload: 22.8 s
+// against 24.0 s for 8-warp CTAs at 2 per SM (16 warps, 125 registers) and
+// 27.3 s at 3 per SM (80 registers, spilling); with later versions of the
+// loop, 16.5 s against 18.2 s at 4 per SM (126 registers), and 15.8 s
+// against 17.4 s at 6 per SM (80 registers, spilling)
 constexpr int kDThreads = 128;
 constexpr int kDWarps = kDThreads / 32;
 constexpr int kCombo = 64;         // (xa, xb, xt) with each count below 4
