@@ -27,25 +27,45 @@ __device__ __forceinline__ int ternary_code(int A, int B, int C, int x, int y, i
          729 * region_state(t, theta);
 }
 
-// Per-lane run-length cache in front of a shared histogram: consecutive
-// instances of the same motif on a lane cost one register add.
-struct RunCache {
+// h[id] += v on a 64-bit bin in shared memory, as a 32-bit atomic add on its
+// low word plus, when that add carries out or v is negative, an add of the
+// carry and v's high word to the high word.  The bin is exact once every add
+// has completed (it is only read after a barrier).
+__device__ __forceinline__ void shared_bin_add(unsigned long long* h, int id, long long v) {
+  unsigned int* w = reinterpret_cast<unsigned int*>(h + id);
+  const unsigned int u = (unsigned int)v;
+  const unsigned int old = atomicAdd(w, u);
+  const unsigned int adj = (old + u < old ? 1u : 0u) + (unsigned int)((unsigned long long)v >> 32);
+  if (adj) atomicAdd(w + 1, adj);
+}
+
+// Per-lane run-length cache in front of a histogram: consecutive instances
+// of the same motif on a lane cost one register add.  kShared: the
+// histogram is in shared memory, and its 64-bit bins are added through
+// shared_bin_add; otherwise (rows in device memory) by 64-bit atomics.
+template <bool kShared>
+struct RunCacheT {
   int id = -1;
   unsigned long long n = 0;
+  __device__ __forceinline__ void put(unsigned long long* hist) {
+    if (kShared) shared_bin_add(hist, id, (long long)n);
+    else atomicAdd(&hist[id], n);
+  }
   __device__ __forceinline__ void add(int new_id, unsigned long long* hist, unsigned long long c = 1) {
     if (new_id != id) {
-      if (n) atomicAdd(&hist[id], n);
+      if (n) put(hist);
       id = new_id;
       n = 0;
     }
     n += c;
   }
   __device__ __forceinline__ void flush(unsigned long long* hist) {
-    if (n) atomicAdd(&hist[id], n);
+    if (n) put(hist);
     n = 0;
     id = -1;
   }
 };
+using RunCache = RunCacheT<true>;
 
 // |X & Y| for two ascending node lists.
 __device__ __forceinline__ int sorted_overlap(const int32_t* X, int nx, const int32_t* Y, int ny) {

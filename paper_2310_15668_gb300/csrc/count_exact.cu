@@ -165,7 +165,7 @@ k_hyperedge_profile(ExactArgs g, unsigned long long* __restrict__ hp) {
       const uint32_t mask_ba = g.nadj[pa].y;   // nodes of e_b lying in e_a
       const bool b_after_a = (int64_t)b > a;
       unsigned long long* hpb = hp + (int64_t)b * 432;
-      RunCache rcb;
+      RunCacheT<false> rcb;   // rows of e_b's profile in device memory
       for (int64_t q = pa + 1 + lane; q < be; q += 32) {
         const uint2 ebk = g.nadj[q];
         const uint32_t k = ent_id(ebk);

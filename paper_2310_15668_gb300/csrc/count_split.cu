@@ -60,16 +60,9 @@ __device__ inline int class_rep(int c, int theta) {
   return c == 0 ? 1 : c == 1 ? 2 : c == 2 ? 3 : c == 3 ? theta + 2 : theta + 3;
 }
 
-// h[id] += v on a 64-bit bin in shared memory, as a 32-bit atomic add on its
-// low word plus, when that add carries out or v is negative, an add of the
-// carry and v's high word to the high word (bins are only read once every
-// add has completed)
+// h[id] += v on a shared 64-bit bin (see shared_bin_add)
 __device__ __forceinline__ void hadd(unsigned long long* h, int id, long long v) {
-  unsigned int* w = reinterpret_cast<unsigned int*>(h + id);
-  const unsigned int u = (unsigned int)v;
-  const unsigned int old = atomicAdd(w, u);
-  const unsigned int adj = (old + u < old ? 1u : 0u) + (unsigned int)((unsigned long long)v >> 32);
-  if (adj) atomicAdd(w + 1, adj);
+  shared_bin_add(h, id, v);
 }
 
 // One closed instance {a, b, k} with sizes A, B, C, omega_ab = x,
