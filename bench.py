@@ -601,12 +601,13 @@ def run_gpu(args):
         cand = float(st.get("candidates", 0))
         sec = avg[dom] / 1000.0
         achieved = 5.0 * cand / sec / 1e9
-        # the kernel's own loads: three overlap planes of rows a and b, four
-        # size planes and one bitmap word per heavy node of e_a & e_b per word
+        # the kernel's own loads per scanned word: 16 bytes of row a's overlap
+        # planes and adjacency mask, 16 of row b's, 16 of size planes and one
+        # bitmap word per heavy node of e_a & e_b
         words = float(st.get("words_scanned", 0))
         hw = float(st.get("dense_hyperwedges", 0)) or 1.0
         n_t = float(st.get("heavy_bitmaps", 0)) / hw
-        loads = words * 4.0 * (3 + 3 + 4 + n_t)
+        loads = words * 4.0 * (4 + 4 + 4 + n_t)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
                 "traffic": (args.traffic_bytes if args.traffic_bytes is not None else
